@@ -1,0 +1,360 @@
+"""Benchmark: factorizations/s on the single large query
+g = (11,13,17,19,23,29), n = 3000 (|Z| = 72,082,790; 1.73 GB of int32 rows).
+
+One step = the whole hot path over that query: fs_count (uint64 result) and
+fs_enumerate (all rows into a device buffer), i.e. precompute, planner,
+slice walks, consumers, finalisation.  `value` = |Z| per step / device time
+per step (inputs resident, results left on the device); `e2e` = the same
+through the synchronous C ABI with the rows copied back to pinned host memory
+inside the timed region.  The dominant kernel's roofline is the enumerate
+write walk against the measured HBM copy bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs the same query on its
+own GPU (independent replicas: weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "single large query g=(11,13,17,19,23,29), n=3000: fs_count + fs_enumerate (int32 rows)"
+METRIC = "factorizations/s (count & enumerate)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_07989_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    e = rec.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def _oracle_task(args):
+    n, wg, lo, hi = args
+    import oracle
+    rows, _ = oracle.enumerate_range(n, wg, lo, hi)
+    return int(rows.shape[0])
+
+
+def cpu_oracle_run(pool, n, wg, budget_s: float = 30.0):
+    """The oracle's bounded stream (save consumer) over the whole query, cut
+    by the leading coordinate a_1 into independent slices run on all host
+    cores.  Returns (factorizations, seconds, slices_done, slices_total)."""
+    d = len(wg)
+    top = n // wg[0]
+    tasks = []
+    for x in range(top + 1):
+        lo = [x] + [0] * (d - 1)
+        hi = [x + 1] + [0] * (d - 1) if x < top else None
+        tasks.append((n, wg, lo, hi))
+    # heaviest slices (small a_1) first
+    t0 = time.perf_counter()
+    total = 0
+    done = 0
+    for c in pool.imap_unordered(_oracle_task, tasks, chunksize=1):
+        total += c
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return total, dt, done, len(tasks)
+
+
+def make_pool():
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2405_07989_gb300 import workloads
+    n, g = workloads.CONFIG2
+    wg = sorted(g, reverse=True)
+    pool, cores = make_pool()
+    try:
+        for _ in range(args.warmup):
+            cpu_oracle_run(pool, n, wg)
+        times, tot = [], 0
+        for _ in range(args.steps):
+            c, dt, done, ntask = cpu_oracle_run(pool, n, wg)
+            times.append(dt)
+            tot = c
+    finally:
+        pool.close()
+        pool.join()
+    ms = 1000.0 * sum(times) / len(times)
+    value = tot / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "factorizations/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"whole query per step: oracle bounded streams (Algorithm 3.1,"
+                                   f" save consumer) over {ntask} leading-coordinate slices"},
+        "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    ws, rank, local = dist_setup()
+    pool = cores = None
+    if ws == 1 and not args.no_cpu_baseline:
+        pool, cores = make_pool()  # before the first GPU call
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2405_07989_gb300 as fs
+    from paper_2405_07989_gb300 import workloads
+    fs.lib()
+
+    n, g = workloads.CONFIG2
+    d = len(g)
+    Z = fs.fs_count(n, g)
+    row_bytes = d * 4
+    out = torch.empty(Z * d, dtype=torch.int32, device=dev)
+    dc = torch.zeros(2, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fs.fs_count_async(n, g, dc[0:1])
+        fs.fs_enumerate_async(n, g, out, Z, dc[1:2])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(dc[0]) == Z and int(dc[1]) == Z, (int(dc[0]), int(dc[1]), Z)
+
+    # ---- timed region: K steps, L2 flushed between steps (untimed) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local] if cvd else str(local))
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    fs.fs_profile_read()
+    fs.fs_profile_enable(True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    fs.fs_profile_enable(False)
+    prof = fs.fs_profile_read()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(ms_steps) / len(ms_steps)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert int(dc[0]) == Z and int(dc[1]) == Z
+    value = ws * Z / (ms / 1000.0)
+    launches = sum(v[0] for v in prof.values()) // args.steps
+
+    # ---- roofline of the dominant kernel (enumerate write walk) ----
+    peaks, peak_src = measured_peaks()
+    enum_launches, enum_ms = prof.get("pair_enum", (0, 0.0))
+    enum_avg = enum_ms / max(enum_launches, 1)
+    alg_bytes = Z * row_bytes
+    achieved = alg_bytes / (enum_avg / 1000.0) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": "pair_enum", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": recorded_traffic("pair_enum"),
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": enum_avg}
+    breakdown = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+                 for k, v in prof.items()}
+
+    # ---- end to end through the synchronous C ABI, rows copied to the host ----
+    host = torch.empty(Z * d, dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c1 = fs.fs_count(n, g)
+        c2 = fs.fs_enumerate(n, g, out, Z)
+        host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        assert c1 == Z and c2 == Z
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ws * Z / e2e_s, "unit": "factorizations/s",
+           "h2d_bytes_per_step": 2 * d * 4,
+           "d2h_bytes_per_step": Z * row_bytes + 2 * 8 * 16,
+           "ms_per_step": e2e_s * 1000.0}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----
+    cpu = None
+    if pool is not None:
+        wg = sorted(g, reverse=True)
+        c, dt, done, ntask = cpu_oracle_run(pool, n, wg)
+        pool.close()
+        pool.join()
+        cpu = {"value": c / dt, "unit": "factorizations/s", "cores": cores, "kind": "oracle",
+               "sample": (f"{done}/{ntask} leading-coordinate slices of the same query "
+                          f"({c} factorizations): oracle bounded streams, Algorithm 3.1, save "
+                          f"consumer, one slice per process ({cores} spawn processes)")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "factorizations/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "factorizations_per_step": Z,
+                       "output_bytes": alg_bytes, "l2": "flushed between steps (256 MB write)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "breakdown": breakdown,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * fs.h -- C ABI of the GB300 factorization-set library.
+ *
+ * The library computes over the factorization set of an element n in the
+ * (not necessarily minimal, coprime or ordered) generators g_1..g_d:
+ *
+ *     Z(n, (g_1..g_d)) = { (a_1..a_d) in N^d : a_1 g_1 + ... + a_d g_d = n }   (Sec. 1)
+ *
+ * by the paper's method: the lexicographic order on N^d is cut into bounded
+ * slices [lo, hi) (Sec. 4), and each GPU worker walks the candidates of its
+ * slice with the nextCandidate successor (Algorithm 3.1).  The consumers are
+ * the ones Sec. 2 lists -- count, predicate, save (enumerate) -- plus length
+ * statistics of sum a_i.  All arithmetic is exact integer arithmetic.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - n      : the element, 0 <= n, and n + max(g) <= 2^31 - 1 (else FS_E_OVERFLOW).
+ * - gens   : HOST pointer to d generators, each >= 1 (a zero generator makes Z
+ *            infinite: FS_E_INVAL).  Repeats, any order, common divisors are
+ *            allowed (Sec. 1 footnote).  The array is read before the call
+ *            returns and never kept.
+ * - d      : 1 <= d <= FS_MAX_D (else FS_E_INVAL).
+ * - stream : a cudaStream_t (NULL = the legacy default stream).  All device
+ *            work is enqueued on it, in stream order with the caller's work.
+ * - device memory passed in (dev_buf, hist_dev, dev_count) is owned by the
+ *   caller and must be resident on the current device; the library never
+ *   frees it.  The library owns only its internal scratch, which it allocates
+ *   on first use per device, grows when needed and keeps until process exit.
+ *   Calls that share a device share that scratch: the library serialises them
+ *   on the host, and asynchronous calls on DIFFERENT streams of one device must
+ *   not overlap on the GPU (order them with events or one stream).
+ * - synchronous calls (no _async suffix) return after their host outputs are
+ *   written; they synchronise `stream`.
+ * - errors: every call returns an fs_status and writes its outputs only on
+ *   FS_OK, except FS_E_CAPACITY (see fs_enumerate).  fs_last_error() gives a
+ *   one-line description of the last failure on the calling thread.
+ * - there is no CPU fallback: without a usable CUDA device every call that
+ *   needs the GPU returns FS_E_CUDA.
+ */
+#ifndef FS_H
+#define FS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FS_MAX_D 16
+
+typedef enum fs_status {
+    FS_OK = 0,
+    FS_E_INVAL = 1,     /* bad argument: d out of range, zero generator, n < 0, NULL pointer */
+    FS_E_OVERFLOW = 2,  /* n + max g >= 2^31, int16 output that cannot hold a coordinate,
+                           or a planner table that would exceed its size limit */
+    FS_E_CAPACITY = 3,  /* enumerate: more factorizations than `cap` */
+    FS_E_NOMEM = 4,     /* device scratch allocation failed */
+    FS_E_CUDA = 5,      /* a CUDA runtime call or kernel launch failed; no device */
+    FS_E_TIMEOUT = 6,   /* a bounded device-side wait ran out */
+    FS_E_NOTIMPL = 7    /* combination not implemented */
+} fs_status;
+
+/* Walk method.  PLAIN runs Algorithm 3.1 exactly: one nextCandidate step per
+ * candidate, consumers filter by wasValid (Sec. 3.2-3.3).  PAIR resolves the
+ * last two coordinates of every prefix in closed form: the congruence step of
+ * Sec. 3.2.4 taken all the way, i.e. jump straight to the first valid value of
+ * a_{d-1} and count / list the valid values of (a_{d-1}, a_d) without visiting
+ * the invalid candidates between them.  Both give identical results. */
+typedef enum fs_method { FS_METHOD_AUTO = 0, FS_METHOD_PLAIN = 1, FS_METHOD_PAIR = 2 } fs_method;
+
+typedef struct fs_config {
+    int32_t method;        /* fs_method; AUTO = PAIR */
+    int32_t keep_order;    /* 1: walk the generators in the caller's order.  0 (default):
+                              walk them in descending order, which visits the fewest
+                              prefixes; the result is the same set (Z does not depend on
+                              the order of the generators, Sec. 1). */
+    int64_t slices;        /* number of lexicographic slices [lo,hi) (Sec. 4); 0 = auto */
+    int32_t block_threads; /* threads per block; 0 = auto */
+    int32_t blocks_per_sm; /* resident blocks per SM for the persistent grid; 0 = auto */
+} fs_config;
+
+/* Fills *cfg with the defaults (all zero = automatic). */
+void fs_config_default(fs_config* cfg);
+
+/* Length statistics of the lengths sum_i a_i over Z (the count is exact).
+ * min_len / max_len are valid only when count > 0 (both 0 otherwise). */
+typedef struct fs_len_summary {
+    uint64_t count;
+    uint32_t min_len;
+    uint32_t max_len;
+} fs_len_summary;
+
+/* A linear predicate on one factorization a, the "predicate" consumer of
+ * Sec. 2.  With s = sum_i w[i] a_i (w in the caller's generator order, int64
+ * arithmetic):
+ *   modulus > 0 : true iff s == c (mod modulus), both sides reduced to [0, modulus)
+ *   op == 0     : true iff s == c
+ *   op == 1     : true iff s <= c
+ *   op == 2     : true iff s >= c
+ * Entries w[d..FS_MAX_D-1] are ignored.  |w[i]| <= 2^20 and |c| <= 2^60. */
+typedef struct fs_predicate {
+    int32_t w[FS_MAX_D];
+    int64_t c;
+    int32_t op;
+    uint32_t modulus;
+} fs_predicate;
+
+/* --- library -------------------------------------------------------------- */
+
+/* Static string naming a status code. */
+const char* fs_status_string(int status);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int fs_version(void);
+/* One-line description of the last failed call on this thread ("" if none).
+ * The pointer stays valid until the next call on this thread. */
+const char* fs_last_error(void);
+
+/* --- the four consumers (Sec. 2), synchronous ----------------------------- */
+
+/* |Z(n, g)| -> *out_count (host).  The count consumer of Sec. 2 over all slices. */
+fs_status fs_count(int64_t n, const uint32_t* gens, int d, uint64_t* out_count, void* stream);
+
+/* Count, min and max of sum a_i -> *out (host).  hist_dev (nullable) is a
+ * DEVICE array of floor(n / min g) + 1 uint64 bins; bin l receives the number of
+ * factorizations of length l (overwritten, not accumulated). */
+fs_status fs_length_stats(int64_t n, const uint32_t* gens, int d, fs_len_summary* out,
+                          uint64_t* hist_dev, void* stream);
+
+/* *out_bool (host) = 1 iff some factorization satisfies *pred (the predicate
+ * consumer of Sec. 2), else 0.  Workers stop early once one is found. */
+fs_status fs_any(int64_t n, const uint32_t* gens, int d, const fs_predicate* pred,
+                 int* out_bool, void* stream);
+
+/* Materialise Z(n, g) (the save consumer of Sec. 2) into dev_buf: a DEVICE
+ * buffer of `cap` rows, row-major [count][d] in the caller's generator order,
+ * each coordinate an int32 (elem_bytes == 4) or int16 (elem_bytes == 2; needs
+ * floor(n / min g) <= 32767, else FS_E_OVERFLOW).  dev_buf must be 16-byte
+ * aligned.  Row order: lexicographically ascending in the walk order of the
+ * generators (descending generators unless cfg->keep_order), deterministic;
+ * with keep_order it is lex-ascending in the caller's order.  *out_count (host)
+ * = |Z|.  If |Z| > cap: returns FS_E_CAPACITY with *out_count = |Z|; the first
+ * cap rows are written, the rest dropped. */
+fs_status fs_enumerate(int64_t n, const uint32_t* gens, int d, void* dev_buf, uint64_t cap,
+                       int elem_bytes, uint64_t* out_count, void* stream);
+
+/* --- the same with an explicit configuration (cfg may be NULL) ----------- */
+
+fs_status fs_count_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                      uint64_t* out_count, void* stream);
+fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                             fs_len_summary* out, uint64_t* hist_dev, void* stream);
+fs_status fs_any_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                    const fs_predicate* pred, int* out_bool, void* stream);
+fs_status fs_enumerate_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                          void* dev_buf, uint64_t cap, int elem_bytes, uint64_t* out_count,
+                          void* stream);
+
+/* --- asynchronous forms: enqueue only, results stay on the device -------- */
+
+/* Enqueues the count; *dev_count (DEVICE uint64) receives |Z| in stream order.
+ * Returns after the launches; argument errors are reported synchronously. */
+fs_status fs_count_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                         uint64_t* dev_count, void* stream);
+
+/* Enqueues the enumeration into dev_buf (as fs_enumerate); *dev_count (DEVICE
+ * uint64) receives |Z|.  Rows past cap are dropped; the caller compares
+ * *dev_count with cap. */
+fs_status fs_enumerate_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                             void* dev_buf, uint64_t cap, int elem_bytes, uint64_t* dev_count,
+                             void* stream);
+
+/* --- slice planner (Sec. 4) ---------------------------------------------- */
+
+/* The slices the walk uses.  A "leaf" is a prefix (a_1..a_{d-2}) of the walk
+ * order with a_1 g_1 + ... + a_{d-2} g_{d-2} <= n; its two last coordinates are
+ * what the PAIR method resolves in closed form.  The planner cuts the
+ * lexicographic order of the leaves into `slices` ranges of (nearly) equal
+ * leaf counts; slice s is the lex range [B_s, B_{s+1}) where B_s is the vector
+ * (leaf, 0, 0) of its first leaf and B_slices = +infinity.
+ *   order   (host, d int32, nullable): walk position k uses caller generator order[k]
+ *   bounds  (host, (slices + 1) x d int32, nullable): row s = B_s in walk order;
+ *           row `slices` is filled with -1 (= +infinity)
+ *   leaves  (host, nullable): total number of leaves
+ * For d <= 2 there is exactly one leaf (the whole set is one slice).
+ * `slices` must be >= 1; slices beyond the number of leaves are empty. */
+fs_status fs_plan(int64_t n, const uint32_t* gens, int d, const fs_config* cfg, int64_t slices,
+                  int32_t* order, int32_t* bounds, uint64_t* leaves);
+
+/* Per-slice counts of the slicing fs_plan describes (same cfg and slices):
+ * counts (host, `slices` uint64) receives |Z intersected with slice s| from the
+ * GPU walk (method per cfg). */
+fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                          int64_t slices, uint64_t* counts, void* stream);
+
+/* --- kernel timing ------------------------------------------------------ */
+
+/* While enabled (on != 0), every kernel the library launches is bracketed by
+ * CUDA events recorded on the stream it is launched on.  Used by benchmarks to
+ * time individual kernels; off by default (no events recorded). */
+void fs_profile_enable(int on);
+
+/* Collects the timings recorded since the last read (waits for their events):
+ * up to `max` entries, one per kernel name, in first-launch order.  names
+ * (host, max * 32 chars, NUL-terminated entries), launches (host, max) = how
+ * many times that kernel ran, total_ms (host, max) = summed device time.
+ * Returns the number of entries (-1 on a CUDA error). */
+int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max);
+
+/* --- host-side self test of the division helper ------------------------- */
+
+/* Checks the library's division by an invariant divisor (Granlund-Montgomery
+ * 1994, round-up multiplier) against C's / and % for divisor `div` and the
+ * numerators x0, x0+1, ..., x0+count-1 (all < 2^31).  Runs on the host, needs
+ * no GPU.  Returns the number of mismatches (0 = correct), -1 on bad input. */
+int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FS_H */

@@ -1,0 +1,266 @@
+"""GB300 factorization sets: Python binding of the C ABI in include/fs.h.
+
+The binding only marshals arguments: every step of the computation runs in
+the CUDA kernels of ``libfs.so``.  There is no CPU fallback; if the library is
+missing or no GPU is usable, calls raise :class:`FsError`.
+
+Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed); the
+stream defaults to torch's current stream.  Function names follow the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfs.so")
+MAX_D = 16
+
+FS_OK, FS_E_INVAL, FS_E_OVERFLOW, FS_E_CAPACITY = 0, 1, 2, 3
+FS_E_NOMEM, FS_E_CUDA, FS_E_TIMEOUT, FS_E_NOTIMPL = 4, 5, 6, 7
+METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+class fs_config(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("keep_order", ctypes.c_int32),
+                ("slices", ctypes.c_int64), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+class fs_len_summary(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32)]
+
+
+class fs_predicate(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32 * MAX_D), ("c", ctypes.c_int64), ("op", ctypes.c_int32),
+                ("modulus", ctypes.c_uint32)]
+
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+_cfgp = ctypes.POINTER(fs_config)
+
+# name -> (restype, argtypes): every entry point declared in include/fs.h
+SIGNATURES = {
+    "fs_config_default": (None, [_cfgp]),
+    "fs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fs_version": (ctypes.c_int, []),
+    "fs_last_error": (ctypes.c_char_p, []),
+    "fs_count": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _u64p, _vp]),
+    "fs_length_stats": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int,
+                                       ctypes.POINTER(fs_len_summary), _vp, _vp]),
+    "fs_any": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int,
+                              ctypes.POINTER(fs_predicate), ctypes.POINTER(ctypes.c_int), _vp]),
+    "fs_enumerate": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _vp, ctypes.c_uint64,
+                                    ctypes.c_int, _u64p, _vp]),
+    "fs_count_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _u64p, _vp]),
+    "fs_length_stats_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
+                                          ctypes.POINTER(fs_len_summary), _vp, _vp]),
+    "fs_any_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
+                                 ctypes.POINTER(fs_predicate), ctypes.POINTER(ctypes.c_int), _vp]),
+    "fs_enumerate_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp,
+                                       ctypes.c_uint64, ctypes.c_int, _u64p, _vp]),
+    "fs_count_async": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp, _vp]),
+    "fs_enumerate_async": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp,
+                                          ctypes.c_uint64, ctypes.c_int, _vp, _vp]),
+    "fs_plan": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, ctypes.c_int64,
+                               _i32p, _i32p, _u64p]),
+    "fs_slice_counts": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
+                                       ctypes.c_int64, _u64p, _vp]),
+    "fs_profile_enable": (None, [ctypes.c_int]),
+    "fs_profile_read": (ctypes.c_int, [ctypes.c_char_p, _u64p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_int]),
+    "fs_selftest_division": (ctypes.c_int64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
+}
+
+
+def status_name(s: int) -> str:
+    names = ["FS_OK", "FS_E_INVAL", "FS_E_OVERFLOW", "FS_E_CAPACITY", "FS_E_NOMEM",
+             "FS_E_CUDA", "FS_E_TIMEOUT", "FS_E_NOTIMPL"]
+    return names[s] if 0 <= s < len(names) else f"FS_E_{s}"
+
+
+def lib():
+    """Load libfs.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+            if _build.stale():
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise FsError(FS_E_CUDA, f"{LIB_PATH} is missing: the CUDA library was not built")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != FS_OK:
+        raise FsError(st, lib().fs_last_error().decode())
+
+
+def _gens(gens):
+    g = [int(x) for x in gens]
+    arr = (ctypes.c_uint32 * max(len(g), 1))(*[x & 0xffffffff for x in g])
+    return arr, len(g)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def make_config(method: int = METHOD_AUTO, keep_order: bool = False, slices: int = 0,
+                block_threads: int = 0, blocks_per_sm: int = 0) -> fs_config:
+    return fs_config(int(method), int(bool(keep_order)), int(slices), int(block_threads),
+                     int(blocks_per_sm))
+
+
+def _cfgp_of(cfg):
+    return ctypes.byref(cfg) if cfg is not None else None
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fs_version() -> int:
+    return lib().fs_version()
+
+
+def fs_count(n: int, gens, cfg: fs_config | None = None, stream=None) -> int:
+    """|Z(n, gens)| (fs_count_ex)."""
+    g, d = _gens(gens)
+    out = ctypes.c_uint64(0)
+    _check(lib().fs_count_ex(int(n), g, d, _cfgp_of(cfg), ctypes.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def fs_count_async(n: int, gens, dev_count, cfg: fs_config | None = None, stream=None) -> None:
+    """Enqueue the count; dev_count is a CUDA uint64/int64 tensor of >= 1 element."""
+    g, d = _gens(gens)
+    _check(lib().fs_count_async(int(n), g, d, _cfgp_of(cfg), _ptr(dev_count), _stream(stream)))
+
+
+def fs_length_stats(n: int, gens, hist=None, cfg: fs_config | None = None, stream=None):
+    """(count, min_len, max_len); hist (optional) is a CUDA int64 tensor of
+    floor(n / min g) + 1 bins, overwritten with the length histogram."""
+    g, d = _gens(gens)
+    out = fs_len_summary()
+    _check(lib().fs_length_stats_ex(int(n), g, d, _cfgp_of(cfg), ctypes.byref(out), _ptr(hist),
+                                    _stream(stream)))
+    return int(out.count), int(out.min_len), int(out.max_len)
+
+
+def fs_any(n: int, gens, w, c: int, op: int = 0, modulus: int = 0,
+           cfg: fs_config | None = None, stream=None) -> bool:
+    """True iff some factorization a has sum w_i a_i (==, <=, >= by op) c, or
+    sum w_i a_i == c (mod modulus) when modulus > 0."""
+    g, d = _gens(gens)
+    p = fs_predicate()
+    for i, x in enumerate(list(w)[:MAX_D]):
+        p.w[i] = int(x)
+    p.c = int(c)
+    p.op = int(op)
+    p.modulus = int(modulus)
+    out = ctypes.c_int(0)
+    _check(lib().fs_any_ex(int(n), g, d, _cfgp_of(cfg), ctypes.byref(p), ctypes.byref(out),
+                           _stream(stream)))
+    return bool(out.value)
+
+
+def fs_enumerate(n: int, gens, out, cap: int | None = None, elem_bytes: int = 4,
+                 cfg: fs_config | None = None, stream=None, allow_capacity: bool = False) -> int:
+    """Write Z(n, gens) into the CUDA tensor `out` (rows [count][d] of int32 or
+    int16); returns |Z|.  cap defaults to the rows `out` holds."""
+    g, d = _gens(gens)
+    if cap is None:
+        cap = out.numel() // max(d, 1) if out is not None else 0
+    cnt = ctypes.c_uint64(0)
+    st = lib().fs_enumerate_ex(int(n), g, d, _cfgp_of(cfg), _ptr(out), int(cap), int(elem_bytes),
+                               ctypes.byref(cnt), _stream(stream))
+    if st == FS_E_CAPACITY and allow_capacity:
+        return int(cnt.value)
+    _check(st)
+    return int(cnt.value)
+
+
+def fs_enumerate_async(n: int, gens, out, cap: int, dev_count, elem_bytes: int = 4,
+                       cfg: fs_config | None = None, stream=None) -> None:
+    """Enqueue the enumeration into `out`; |Z| lands in dev_count[0]."""
+    g, d = _gens(gens)
+    _check(lib().fs_enumerate_async(int(n), g, d, _cfgp_of(cfg), _ptr(out), int(cap),
+                                    int(elem_bytes), _ptr(dev_count), _stream(stream)))
+
+
+def fs_plan(n: int, gens, slices: int, cfg: fs_config | None = None):
+    """(order, bounds, leaves): the walk order of the generators, the first
+    vector (leaf, 0, 0) of every slice in walk order (rows of -1 past the last
+    leaf; the last row is +infinity), and the number of leaves."""
+    g, d = _gens(gens)
+    order = (ctypes.c_int32 * d)()
+    bounds = (ctypes.c_int32 * ((slices + 1) * d))()
+    leaves = ctypes.c_uint64(0)
+    _check(lib().fs_plan(int(n), g, d, _cfgp_of(cfg), int(slices), order, bounds,
+                         ctypes.byref(leaves)))
+    rows = [list(bounds[i * d:(i + 1) * d]) for i in range(slices + 1)]
+    return list(order), rows, int(leaves.value)
+
+
+def fs_slice_counts(n: int, gens, slices: int, cfg: fs_config | None = None, stream=None):
+    """Per-slice counts of the slicing fs_plan describes."""
+    g, d = _gens(gens)
+    out = (ctypes.c_uint64 * slices)()
+    _check(lib().fs_slice_counts(int(n), g, d, _cfgp_of(cfg), int(slices), out, _stream(stream)))
+    return [int(x) for x in out]
+
+
+def fs_profile_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (for benchmarks)."""
+    lib().fs_profile_enable(1 if on else 0)
+
+
+def fs_profile_read(max_entries: int = 64):
+    """{kernel name: (launches, total device ms)} recorded since the last read."""
+    names = ctypes.create_string_buffer(32 * max_entries)
+    launches = (ctypes.c_uint64 * max_entries)()
+    ms = (ctypes.c_double * max_entries)()
+    k = lib().fs_profile_read(names, launches, ms, max_entries)
+    if k < 0:
+        raise FsError(FS_E_CUDA, "profile read failed")
+    out = {}
+    for i in range(k):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def fs_selftest_division(div: int, x0: int, count: int) -> int:
+    """Host self test of the invariant-divisor division (no GPU needed)."""
+    return int(lib().fs_selftest_division(int(div), int(x0), int(count)))

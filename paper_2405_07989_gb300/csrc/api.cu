@@ -1,0 +1,760 @@
+// The C ABI (include/fs.h): argument checks, canonical walk order, per-query
+// constants, the device scratch arena, and the launch sequence of each
+// consumer.  Every step of the computation runs in the kernels; this file
+// only validates, lays out memory and enqueues.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "walk.cuh"
+
+using namespace fsi;
+
+namespace {
+
+thread_local std::string t_err;
+
+fs_status fail(fs_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+fs_status cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(FS_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// per-device state: scratch arena and a pinned result buffer
+// ---------------------------------------------------------------------------
+struct DevState {
+    void* arena = nullptr;
+    size_t size = 0;
+    uint64_t* pinned = nullptr;
+    int sms = 0;
+};
+
+std::mutex g_mu;
+std::vector<DevState> g_dev;
+
+fs_status get_dev(DevState** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    DevState& ds = g_dev[dev];
+    if (ds.sms == 0) {
+        e = cudaDeviceGetAttribute(&ds.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        e = cudaMallocHost((void**)&ds.pinned, 4096);
+        if (e != cudaSuccess) {
+            ds.sms = 0;
+            return fail(FS_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = &ds;
+    return FS_OK;
+}
+
+fs_status ensure_arena(DevState* ds, size_t bytes)
+{
+    if (ds->size >= bytes) return FS_OK;
+    if (ds->arena) {
+        cudaDeviceSynchronize();  // earlier work may still use the old arena
+        cudaFree(ds->arena);
+        ds->arena = nullptr;
+        ds->size = 0;
+    }
+    size_t want = std::max(bytes, (size_t)16 << 20);
+    want = (want + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+    cudaError_t e = cudaMalloc(&ds->arena, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ds->arena = nullptr;
+        return fail(FS_E_NOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+    }
+    ds->size = want;
+    return FS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing (fs_profile_enable / fs_profile_read)
+// ---------------------------------------------------------------------------
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+    int kernels;
+};
+bool g_prof = false;
+std::vector<ProfRec> g_prof_pending;
+
+struct ProfScope {
+    ProfRec rec;
+    cudaStream_t st;
+    bool on;
+    ProfScope(const char* name, cudaStream_t s, int kernels) : st(s), on(g_prof && kernels > 0)
+    {
+        if (!on) return;
+        rec.name = name;
+        rec.kernels = kernels;
+        cudaEventCreate(&rec.a);
+        cudaEventCreate(&rec.b);
+        cudaEventRecord(rec.a, st);
+    }
+    ~ProfScope()
+    {
+        if (!on) return;
+        cudaEventRecord(rec.b, st);
+        g_prof_pending.push_back(rec);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// query canonicalisation and constants
+// ---------------------------------------------------------------------------
+int64_t gcd64(int64_t a, int64_t b)
+{
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// inverse of a modulo m (gcd(a, m) = 1, m >= 1) by the extended Euclidean algorithm
+int64_t modinv(int64_t a, int64_t m)
+{
+    if (m == 1) return 0;
+    int64_t r0 = m, r1 = ((a % m) + m) % m, s0 = 0, s1 = 1;
+    while (r1) {
+        int64_t qt = r0 / r1, t = r0 - qt * r1;
+        r0 = r1;
+        r1 = t;
+        t = s0 - qt * s1;
+        s0 = s1;
+        s1 = t;
+    }
+    return ((s0 % m) + m) % m;
+}
+
+struct Query {
+    QueryConst q;
+    std::vector<int> real_levels;  // walk levels with a caller column, in walk order
+};
+
+fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& cfg, Query& Q)
+{
+    if (!gens) return fail(FS_E_INVAL, "gens is NULL");
+    if (d < 1 || d > FS_MAX_D) return fail(FS_E_INVAL, "d = %d outside [1, %d]", d, FS_MAX_D);
+    if (n < 0) return fail(FS_E_INVAL, "n = %lld is negative", (long long)n);
+    uint32_t gmax = 0, gmin = 0xffffffffu;
+    for (int i = 0; i < d; i++) {
+        if (gens[i] == 0) return fail(FS_E_INVAL, "generator %d is zero", i);
+        gmax = std::max(gmax, gens[i]);
+        gmin = std::min(gmin, gens[i]);
+    }
+    if (n + (int64_t)gmax > 2147483647LL)
+        return fail(FS_E_OVERFLOW, "n + max g = %lld exceeds 2^31 - 1", (long long)(n + gmax));
+    QueryConst& q = Q.q;
+    memset(&q, 0, sizeof q);
+    q.n = (int32_t)n;
+    q.d = d;
+    q.D = std::max(d, 3);
+    q.P = q.D - 2;
+    // walk order: caller's order, or descending generators (fewest prefixes)
+    std::vector<int> ord(d);
+    for (int i = 0; i < d; i++) ord[i] = i;
+    if (!cfg.keep_order)
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return gens[a] > gens[b]; });
+    const int32_t virt = (int32_t)n + 1;  // a generator above n: its coordinate is always 0
+    std::vector<int> lev_col(q.D, -1);
+    if (d >= 3) {
+        for (int k = 0; k < d; k++) lev_col[k] = ord[k];
+    } else if (d == 2) {
+        lev_col[1] = ord[0];
+        lev_col[2] = ord[1];
+    } else {
+        lev_col[1] = ord[0];
+    }
+    for (int k = 0; k < FS_MAX_D; k++) {
+        q.col[k] = -1;
+        q.h[k] = 1;
+    }
+    Q.real_levels.clear();
+    for (int k = 0; k < q.D; k++) {
+        q.col[k] = lev_col[k];
+        q.h[k] = lev_col[k] >= 0 ? (int32_t)gens[lev_col[k]] : virt;
+        if (lev_col[k] >= 0) Q.real_levels.push_back(k);
+    }
+    for (int k = 0; k < FS_MAX_D; k++) q.dv_h[k] = make_div32((uint32_t)q.h[k]);
+    // the pair
+    q.A = q.h[q.P];
+    q.B = q.h[q.P + 1];
+    const int64_t G = gcd64(q.A, q.B);
+    q.G = (int32_t)G;
+    q.u = (int32_t)(q.A / G);
+    q.v = (int32_t)(q.B / G);
+    q.inv = (int32_t)modinv(q.u, q.v);
+    q.delta = q.v - q.u;
+    const uint64_t lcm = (uint64_t)q.u * (uint64_t)q.B;
+    q.tab_e = lcm <= (uint64_t)TABLE_E_MAX;
+    q.tab_xy = lcm <= (uint64_t)TABLE_XY_MAX;
+    q.lcm = (q.tab_e || q.tab_xy) ? (uint32_t)lcm : 0;
+    if (q.lcm) q.dv_lcm = make_div32(q.lcm);
+    q.dv_in = make_div32((uint32_t)q.h[q.P - 1]);
+    q.dv_A = make_div32((uint32_t)q.A);
+    q.dv_B = make_div32((uint32_t)q.B);
+    q.dv_G = make_div32((uint32_t)q.G);
+    q.dv_v = make_div32((uint32_t)q.v);
+    q.maxlen = (int32_t)(n / gmin);
+    q.dbins = q.maxlen + std::abs(q.delta) + 1;
+    q.nw = q.P - 1;
+    // planner tables: nw * (n + 1) uint64
+    const double wbytes = (double)q.nw * (double)(n + 1) * 8.0;
+    if (wbytes > 8.0 * (1ull << 30))
+        return fail(FS_E_OVERFLOW, "leaf-count tables would take %.1f GiB (limit 8 GiB)",
+                    wbytes / (1ull << 30));
+    return FS_OK;
+}
+
+fs_status build_pred(const Query& Q, const fs_predicate* p, PredConst& pc)
+{
+    const QueryConst& q = Q.q;
+    if (!p) return fail(FS_E_INVAL, "predicate is NULL");
+    if (p->modulus == 0 && (p->op < 0 || p->op > 2))
+        return fail(FS_E_INVAL, "predicate op %d outside {0,1,2}", p->op);
+    if (p->c > (1ll << 60) || p->c < -(1ll << 60)) return fail(FS_E_INVAL, "|c| > 2^60");
+    if (p->modulus > 0x7fffffffu) return fail(FS_E_INVAL, "modulus >= 2^31");
+    memset(&pc, 0, sizeof pc);
+    for (int k = 0; k < q.D; k++) {
+        int c = q.col[k];
+        if (c >= 0) {
+            int32_t w = p->w[c];
+            if (w > (1 << 20) || w < -(1 << 20)) return fail(FS_E_INVAL, "|w[%d]| > 2^20", c);
+            pc.w[k] = w;
+        }
+    }
+    pc.c = p->c;
+    pc.op = p->op;
+    pc.modulus = (int32_t)p->modulus;
+    pc.dw = pc.w[q.P] * (int64_t)q.v - pc.w[q.P + 1] * (int64_t)q.u;
+    if (pc.modulus > 0) {
+        const int64_t M = pc.modulus;
+        const int64_t dm = ((pc.dw % M) + M) % M;
+        pc.gM = dm == 0 ? M : gcd64(dm, M);
+        pc.Mq = M / pc.gM;
+        pc.invq = modinv(dm / pc.gM, pc.Mq);
+    }
+    return FS_OK;
+}
+
+fs_config cfg_or_default(const fs_config* cfg)
+{
+    fs_config c;
+    memset(&c, 0, sizeof c);
+    if (cfg) c = *cfg;
+    return c;
+}
+
+int method_of(const fs_config& c)
+{
+    return c.method == FS_METHOD_PLAIN ? FS_METHOD_PLAIN : FS_METHOD_PAIR;
+}
+
+// ---------------------------------------------------------------------------
+// launch geometry and scratch layout
+// ---------------------------------------------------------------------------
+fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method, int eb, int sms,
+                   LaunchCfg& lc)
+{
+    cudaError_t e;
+    int bps = 0;
+    if (method == FS_METHOD_PLAIN) {
+        lc.threads = 128;
+        e = plain_occupancy(q, op, lc.threads, &bps);
+    } else {
+        int t = cfg.block_threads > 0 ? cfg.block_threads : 256;
+        if (t % 32 != 0 || t > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", t);
+        lc.threads = t;
+        e = pair_occupancy(q, op, lc.threads, eb, &bps);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (bps < 1) return fail(FS_E_CUDA, "kernel does not fit on an SM");
+    if (cfg.blocks_per_sm > 0) bps = std::min(bps, cfg.blocks_per_sm);
+    lc.blocks = sms * bps;
+    uint64_t S;
+    if (cfg.slices > 0) S = (uint64_t)cfg.slices;
+    else if (method == FS_METHOD_PLAIN) S = (uint64_t)lc.blocks * lc.threads * 2;
+    else S = (uint64_t)lc.blocks * (lc.threads / 32) * 8;
+    if (S > (1ull << 31)) return fail(FS_E_INVAL, "slices = %llu exceeds 2^31", (unsigned long long)S);
+    lc.S = S;
+    return FS_OK;
+}
+
+struct Layout {
+    size_t ctr, W, E, X0, YD, cnt, off, D, extra, total;
+};
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes)
+{
+    Layout L;
+    size_t p = 0;
+    L.ctr = p;
+    p = al(p + CTR_N * 8);
+    L.W = p;
+    p = al(p + (size_t)q.nw * (size_t)(q.n + 1) * 8);
+    L.E = p;
+    p = al(p + (q.tab_e ? q.lcm : 0));
+    L.X0 = p;
+    p = al(p + (q.tab_xy ? (size_t)q.lcm * 4 : 0));
+    L.YD = p;
+    p = al(p + (q.tab_xy ? (size_t)q.lcm * 4 : 0));
+    L.cnt = p;
+    p = al(p + (size_t)S * 8);
+    L.off = p;
+    p = al(p + (size_t)(S + 1) * 8);
+    L.D = p;
+    p = al(p + (size_t)std::max(q.dbins, q.maxlen + 1) * 8);
+    L.extra = p;
+    p = al(p + extra_bytes);
+    L.total = p;
+    return L;
+}
+
+Scratch scratch_at(void* base, const Layout& L)
+{
+    char* b = (char*)base;
+    Scratch s;
+    s.ctr = (uint64_t*)(b + L.ctr);
+    s.W = (uint64_t*)(b + L.W);
+    s.E = (int8_t*)(b + L.E);
+    s.X0 = (int32_t*)(b + L.X0);
+    s.YD = (int32_t*)(b + L.YD);
+    s.slice_cnt = (uint64_t*)(b + L.cnt);
+    s.slice_off = (uint64_t*)(b + L.off);
+    s.D = (uint64_t*)(b + L.D);
+    return s;
+}
+
+const char* walk_name(Op op, int method)
+{
+    static const char* pair[] = {"pair_count", "pair_slice_count", "pair_len", "pair_any", "pair_enum"};
+    static const char* plain[] = {"plain_count", "plain_slice_count", "plain_len", "plain_any",
+                                  "plain_enum"};
+    return method == FS_METHOD_PLAIN ? plain[op] : pair[op];
+}
+
+cudaError_t launch_walk(const QueryConst& q, const Scratch& sc, Op op, int method, const LaunchCfg& lc,
+                        int queue, const PredConst* pred, void* out, uint64_t cap, int eb,
+                        cudaStream_t st)
+{
+    ProfScope ps(walk_name(op, method), st, 1);
+    if (method == FS_METHOD_PLAIN) return launch_plain(q, sc, op, lc, queue, pred, out, cap, eb, st);
+    return launch_pair(q, sc, op, lc, queue, pred, out, cap, eb, st);
+}
+
+// Everything a call enqueues: precompute, walk(s), finalisation.
+struct Call {
+    Query Q;
+    fs_config cfg;
+    int method = FS_METHOD_PAIR;
+    DevState* ds = nullptr;
+    Scratch sc;
+    Layout L;
+    LaunchCfg lc;
+    cudaStream_t st = nullptr;
+};
+
+fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_config* cfg, Op op,
+                  int eb, void* stream, size_t extra_bytes = 0)
+{
+    c.cfg = cfg_or_default(cfg);
+    c.method = method_of(c.cfg);
+    c.st = (cudaStream_t)stream;
+    fs_status s = build_query(n, gens, d, c.cfg, c.Q);
+    if (s != FS_OK) return s;
+    s = get_dev(&c.ds);
+    if (s != FS_OK) return s;
+    // the enumerate count walk and write walk share the slicing: take the
+    // geometry of the write walk for both
+    s = geometry(c.Q.q, c.cfg, op == OP_ENUM && c.method == FS_METHOD_PAIR ? OP_ENUM : op, c.method,
+                 eb, c.ds->sms, c.lc);
+    if (s != FS_OK) return s;
+    c.L = make_layout(c.Q.q, c.lc.S, extra_bytes);
+    s = ensure_arena(c.ds, c.L.total);
+    if (s != FS_OK) return s;
+    c.sc = scratch_at(c.ds->arena, c.L);
+    cudaError_t e = cudaMemsetAsync(c.sc.ctr, 0, CTR_N * 8, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    {
+        const QueryConst& q = c.Q.q;
+        ProfScope ps("precompute", c.st, ((q.tab_e || q.tab_xy) ? 1 : 0) + (q.nw > 0 ? 1 : 0));
+        e = launch_precompute(q, c.sc, c.st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    return FS_OK;
+}
+
+fs_status read_ctr(Call& c)
+{
+    cudaError_t e = cudaMemcpyAsync(c.ds->pinned, c.sc.ctr, CTR_N * 8, cudaMemcpyDeviceToHost, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel execution");
+    if (c.ds->pinned[CTR_ERR] != 0)
+        return fail(FS_E_CUDA, "internal error: a slice walk ran past the last leaf (flags %llx)",
+                    (unsigned long long)c.ds->pinned[CTR_ERR]);
+    return FS_OK;
+}
+
+fs_status do_count(Call& c, uint64_t* dev_count)
+{
+    LaunchCfg lc = c.lc;
+    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_COUNT, c.method, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "count launch");
+    if (dev_count) {
+        ProfScope ps("copy_result", c.st, 1);
+        e = launch_copy_u64(c.sc.ctr + CTR_COUNT, dev_count, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy launch");
+    }
+    return FS_OK;
+}
+
+fs_status do_enum(Call& c, void* dev_buf, uint64_t cap, int eb, uint64_t* dev_count)
+{
+    // first walk: per-slice counts; scan: per-slice offsets; second walk: rows
+    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, eb, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "enumerate count launch");
+    {
+        ProfScope ps("scan_slices", c.st, 1);
+        e = launch_scan_slices(c.sc, c.lc.S, dev_count, c.st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "scan launch");
+    if (cap > 0) {
+        e = launch_walk(c.Q.q, c.sc, OP_ENUM, c.method, c.lc, CTR_QUEUE2, nullptr, dev_buf, cap, eb, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "enumerate write launch");
+    }
+    return FS_OK;
+}
+
+fs_status check_enum_args(const Query& Q, void* dev_buf, uint64_t cap, int eb)
+{
+    if (eb != 2 && eb != 4) return fail(FS_E_INVAL, "elem_bytes = %d, need 2 or 4", eb);
+    if (cap > 0 && !dev_buf) return fail(FS_E_INVAL, "dev_buf is NULL");
+    if (((uintptr_t)dev_buf & 15) != 0) return fail(FS_E_INVAL, "dev_buf is not 16-byte aligned");
+    if (eb == 2 && Q.q.maxlen > 32767)
+        return fail(FS_E_OVERFLOW, "int16 output: a coordinate can reach %d", Q.q.maxlen);
+    if (cap > (~0ull) / (uint64_t)Q.q.d / 4) return fail(FS_E_INVAL, "cap too large");
+    return FS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fs_config_default(fs_config* cfg)
+{
+    if (cfg) memset(cfg, 0, sizeof *cfg);
+}
+
+const char* fs_status_string(int s)
+{
+    switch (s) {
+    case FS_OK: return "FS_OK";
+    case FS_E_INVAL: return "FS_E_INVAL";
+    case FS_E_OVERFLOW: return "FS_E_OVERFLOW";
+    case FS_E_CAPACITY: return "FS_E_CAPACITY";
+    case FS_E_NOMEM: return "FS_E_NOMEM";
+    case FS_E_CUDA: return "FS_E_CUDA";
+    case FS_E_TIMEOUT: return "FS_E_TIMEOUT";
+    case FS_E_NOTIMPL: return "FS_E_NOTIMPL";
+    }
+    return "FS_E_UNKNOWN";
+}
+
+int fs_version(void) { return 100; }
+
+const char* fs_last_error(void) { return t_err.c_str(); }
+
+fs_status fs_count_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                      uint64_t* out_count, void* stream)
+{
+    if (!out_count) return fail(FS_E_INVAL, "out_count is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_COUNT, 4, stream);
+    if (s == FS_OK) s = do_count(c, nullptr);
+    if (s == FS_OK) s = read_ctr(c);
+    if (s == FS_OK) *out_count = c.ds->pinned[CTR_COUNT];
+    return s;
+}
+
+fs_status fs_count(int64_t n, const uint32_t* gens, int d, uint64_t* out_count, void* stream)
+{
+    return fs_count_ex(n, gens, d, nullptr, out_count, stream);
+}
+
+fs_status fs_count_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                         uint64_t* dev_count, void* stream)
+{
+    if (!dev_count) return fail(FS_E_INVAL, "dev_count is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_COUNT, 4, stream);
+    if (s == FS_OK) s = do_count(c, dev_count);
+    return s;
+}
+
+fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                             fs_len_summary* out, uint64_t* hist_dev, void* stream)
+{
+    if (!out) return fail(FS_E_INVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_LEN, 4, stream);
+    if (s != FS_OK) return s;
+    const QueryConst& q = c.Q.q;
+    cudaError_t e = cudaMemsetAsync(c.sc.D, 0, (size_t)std::max(q.dbins, q.maxlen + 1) * 8, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = launch_walk(q, c.sc, OP_LEN, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "length launch");
+    const int stride = c.method == FS_METHOD_PLAIN ? 0 : std::abs(q.delta);
+    {
+        ProfScope ps("len_finalize", c.st, 1);
+        e = launch_len_finalize(q, c.sc, hist_dev, stride, c.st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+    s = read_ctr(c);
+    if (s != FS_OK) return s;
+    out->count = c.ds->pinned[CTR_COUNT];
+    if (out->count > 0) {
+        out->min_len = (uint32_t)(0xffffffffu - c.ds->pinned[CTR_MINC]);
+        out->max_len = (uint32_t)c.ds->pinned[CTR_MAX];
+    } else {
+        out->min_len = out->max_len = 0;
+    }
+    return FS_OK;
+}
+
+fs_status fs_length_stats(int64_t n, const uint32_t* gens, int d, fs_len_summary* out,
+                          uint64_t* hist_dev, void* stream)
+{
+    return fs_length_stats_ex(n, gens, d, nullptr, out, hist_dev, stream);
+}
+
+fs_status fs_any_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                    const fs_predicate* pred, int* out_bool, void* stream)
+{
+    if (!out_bool) return fail(FS_E_INVAL, "out_bool is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Call c;
+    fs_config cc = cfg_or_default(cfg);
+    // validate the predicate before any device work
+    {
+        Query Q;
+        fs_status s = build_query(n, gens, d, cc, Q);
+        if (s != FS_OK) return s;
+        PredConst pc;
+        s = build_pred(Q, pred, pc);
+        if (s != FS_OK) return s;
+    }
+    fs_status s = prepare(c, n, gens, d, cfg, OP_ANY, 4, stream);
+    if (s != FS_OK) return s;
+    PredConst pc;
+    s = build_pred(c.Q, pred, pc);
+    if (s != FS_OK) return s;
+    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_ANY, c.method, c.lc, CTR_QUEUE, &pc, nullptr, 0, 4, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "any launch");
+    s = read_ctr(c);
+    if (s == FS_OK) *out_bool = c.ds->pinned[CTR_FOUND] ? 1 : 0;
+    return s;
+}
+
+fs_status fs_any(int64_t n, const uint32_t* gens, int d, const fs_predicate* pred, int* out_bool,
+                 void* stream)
+{
+    return fs_any_ex(n, gens, d, nullptr, pred, out_bool, stream);
+}
+
+fs_status fs_enumerate_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                          void* dev_buf, uint64_t cap, int elem_bytes, uint64_t* out_count,
+                          void* stream)
+{
+    if (!out_count) return fail(FS_E_INVAL, "out_count is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    {
+        Query Q;
+        fs_status s = build_query(n, gens, d, cfg_or_default(cfg), Q);
+        if (s != FS_OK) return s;
+        s = check_enum_args(Q, dev_buf, cap, elem_bytes);
+        if (s != FS_OK) return s;
+    }
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_ENUM, elem_bytes, stream);
+    if (s == FS_OK) s = do_enum(c, dev_buf, cap, elem_bytes, nullptr);
+    if (s == FS_OK) s = read_ctr(c);
+    if (s != FS_OK) return s;
+    *out_count = c.ds->pinned[CTR_TOTAL];
+    if (*out_count > cap)
+        return fail(FS_E_CAPACITY, "%llu factorizations, capacity %llu",
+                    (unsigned long long)*out_count, (unsigned long long)cap);
+    return FS_OK;
+}
+
+fs_status fs_enumerate(int64_t n, const uint32_t* gens, int d, void* dev_buf, uint64_t cap,
+                       int elem_bytes, uint64_t* out_count, void* stream)
+{
+    return fs_enumerate_ex(n, gens, d, nullptr, dev_buf, cap, elem_bytes, out_count, stream);
+}
+
+fs_status fs_enumerate_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                             void* dev_buf, uint64_t cap, int elem_bytes, uint64_t* dev_count,
+                             void* stream)
+{
+    if (!dev_count) return fail(FS_E_INVAL, "dev_count is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    {
+        Query Q;
+        fs_status s = build_query(n, gens, d, cfg_or_default(cfg), Q);
+        if (s != FS_OK) return s;
+        s = check_enum_args(Q, dev_buf, cap, elem_bytes);
+        if (s != FS_OK) return s;
+    }
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_ENUM, elem_bytes, stream);
+    if (s == FS_OK) s = do_enum(c, dev_buf, cap, elem_bytes, dev_count);
+    return s;
+}
+
+fs_status fs_plan(int64_t n, const uint32_t* gens, int d, const fs_config* cfg, int64_t slices,
+                  int32_t* order, int32_t* bounds, uint64_t* leaves)
+{
+    if (slices < 1 || slices > (1ll << 31)) return fail(FS_E_INVAL, "slices = %lld", (long long)slices);
+    std::lock_guard<std::mutex> lk(g_mu);
+    fs_config cc = cfg_or_default(cfg);
+    cc.slices = slices;
+    Call c;
+    const size_t extra = (size_t)slices * FS_MAX_D * 4;
+    fs_status s = prepare(c, n, gens, d, &cc, OP_SLICES, 4, nullptr, extra);
+    if (s != FS_OK) return s;
+    const QueryConst& q = c.Q.q;
+    int32_t* dbounds = (int32_t*)((char*)c.ds->arena + c.L.extra);
+    cudaError_t e = launch_plan_bounds(q, c.sc, (uint64_t)slices, dbounds, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "plan launch");
+    std::vector<int32_t> hb((size_t)slices * q.D);
+    e = cudaMemcpyAsync(hb.data(), dbounds, hb.size() * 4, cudaMemcpyDeviceToHost, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    if (q.P > 1) {
+        e = cudaMemcpyAsync(c.ds->pinned, c.sc.W + q.n, 8, cudaMemcpyDeviceToHost, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "plan execution");
+    uint64_t L = q.P == 1 ? (uint64_t)(q.n / q.h[0]) + 1 : c.ds->pinned[0];
+    if (leaves) *leaves = L;
+    const int nr = (int)c.Q.real_levels.size();
+    if (order)
+        for (int j = 0; j < nr; j++) order[j] = q.col[c.Q.real_levels[j]];
+    if (bounds) {
+        for (int64_t sl = 0; sl < slices; sl++)
+            for (int j = 0; j < nr; j++) bounds[sl * d + j] = hb[(size_t)sl * q.D + c.Q.real_levels[j]];
+        for (int j = 0; j < d; j++) bounds[slices * d + j] = -1;
+    }
+    return FS_OK;
+}
+
+fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                          int64_t slices, uint64_t* counts, void* stream)
+{
+    if (!counts) return fail(FS_E_INVAL, "counts is NULL");
+    if (slices < 1 || slices > (1ll << 31)) return fail(FS_E_INVAL, "slices = %lld", (long long)slices);
+    std::lock_guard<std::mutex> lk(g_mu);
+    fs_config cc = cfg_or_default(cfg);
+    cc.slices = slices;
+    Call c;
+    fs_status s = prepare(c, n, gens, d, &cc, OP_SLICES, 4, stream);
+    if (s != FS_OK) return s;
+    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice count launch");
+    e = cudaMemcpyAsync(counts, c.sc.slice_cnt, (size_t)slices * 8, cudaMemcpyDeviceToHost, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice count execution");
+    return FS_OK;
+}
+
+void fs_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prof = on != 0;
+}
+
+int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<uint64_t, double>> acc;
+    int rc = 0;
+    for (ProfRec& r : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+            rc = -1;
+        if (!acc.count(r.name)) order.push_back(r.name);
+        acc[r.name].first += (uint64_t)r.kernels;
+        acc[r.name].second += ms;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_pending.clear();
+    if (rc < 0) {
+        cudaGetLastError();
+        return -1;
+    }
+    int k = 0;
+    for (const std::string& nm : order) {
+        if (k >= max) break;
+        if (names) {
+            strncpy(names + 32 * k, nm.c_str(), 31);
+            names[32 * k + 31] = 0;
+        }
+        if (launches) launches[k] = acc[nm].first;
+        if (total_ms) total_ms[k] = acc[nm].second;
+        k++;
+    }
+    return k;
+}
+
+int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count)
+{
+    if (div == 0 || div > 0x7fffffffu) return -1;
+    if ((uint64_t)x0 + count > 0x80000000ull) return -1;
+    const Div32 q = make_div32(div);
+    int64_t bad = 0;
+    for (uint64_t x = x0; x < (uint64_t)x0 + count; x++) {
+        uint32_t qq = div32((uint32_t)x, q);
+        uint32_t rr = (uint32_t)x - qq * div;
+        if (qq != (uint32_t)x / div || rr != (uint32_t)x % div) bad++;
+    }
+    return bad;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Internal definitions shared by the CUDA translation units of the library.
+//
+// Walk layout.  The walk uses D = max(d, 3) "levels".  Levels 0..P-1 (P = D-2)
+// are the prefix levels: a prefix (a_0..a_{P-1}) with phi <= n is a LEAF.  Levels
+// P and P+1 hold the pair (A, B) that the PAIR method resolves in closed form.
+// Level P-1 is the innermost prefix level; the prefixes of levels 0..P-2 are
+// RUNS (a run is the sequence of leaves a_{P-1} = 0, 1, ... under one run
+// prefix).  For d < 3, virtual levels with generator n+1 (so their coordinate is
+// always 0) pad the walk to 3 levels; they have no output column.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/fs.h"
+
+#if defined(__CUDACC__)
+#define FS_HD __host__ __device__ __forceinline__
+#define FS_D __device__ __forceinline__
+#else
+#define FS_HD inline
+#define FS_D inline
+#endif
+
+namespace fsi {
+
+// ---------------------------------------------------------------------------
+// Division by an invariant divisor.
+//
+// Granlund & Montgomery, "Division by invariant integers using multiplication"
+// (PLDI 1994), Thm 4.2: if 2^(N+l) <= m*dv <= 2^(N+l) + 2^l then
+// floor(x/dv) = floor(m*x / 2^(N+l)) for all 0 <= x < 2^N.  With N = 31,
+// l = ceil(log2 dv) and m = ceil(2^(31+l) / dv) both inequalities hold and
+// m < 2^32, so one 32x32->64 multiply and one 64-bit shift divide any
+// x < 2^31 exactly.
+// ---------------------------------------------------------------------------
+struct Div32 {
+    uint32_t m;
+    uint32_t s;   // 31 + l
+    uint32_t dv;
+};
+
+inline Div32 make_div32(uint32_t dv)
+{
+    uint32_t l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < dv) l++;
+    Div32 r;
+    r.s = 31 + l;
+    r.m = (uint32_t)((((uint64_t)1 << r.s) + dv - 1) / dv);
+    r.dv = dv;
+    return r;
+}
+
+FS_HD uint32_t div32(uint32_t x, const Div32& q)
+{
+    return (uint32_t)(((uint64_t)x * q.m) >> q.s);
+}
+
+// ---------------------------------------------------------------------------
+// Per-query constants, computed on the host from (n, g) and passed to every
+// kernel by value.  Tables that depend on n (leaf weights) or on lcm(A, B)
+// (pair tables) are built on the device from these constants.
+// ---------------------------------------------------------------------------
+enum { TABLE_E_MAX = 16384, TABLE_XY_MAX = 4096 };
+
+struct QueryConst {
+    int32_t n;            // the element
+    int32_t d;            // caller's dimension
+    int32_t D;            // walk levels, max(d, 3)
+    int32_t P;            // prefix levels, D - 2 (>= 1)
+    int32_t h[FS_MAX_D];  // generator of each walk level
+    int32_t col[FS_MAX_D];// caller column of each walk level, -1 for a virtual level
+    // the pair: A = h[P], B = h[P+1]
+    int32_t A, B;
+    int32_t G;            // gcd(A, B)
+    int32_t u, v;         // A / G, B / G
+    int32_t inv;          // u^-1 mod v (0 if v == 1)
+    int32_t delta;        // v - u: change of a_P + a_{P+1} per step t of the pair
+    uint32_t lcm;         // lcm(A, B) when a table path is possible, else 0
+    int32_t tab_e;        // 1: the count table E[lcm] is used
+    int32_t tab_xy;       // 1: the tables X0[lcm], YD[lcm] are used
+    Div32 dv_lcm, dv_in, dv_A, dv_B, dv_G, dv_v;
+    Div32 dv_h[FS_MAX_D]; // per level, for the PLAIN method's decrementAndSolve
+    int32_t maxlen;       // floor(n / min real g): the largest possible length
+    int32_t dbins;        // histogram difference-array size: maxlen + |delta| + 1
+    int32_t nw;           // number of leaf-weight tables: P - 1
+    int32_t pad0;
+};
+
+// ---------------------------------------------------------------------------
+// Device scratch layout of one call (byte offsets into the scratch arena).
+// ---------------------------------------------------------------------------
+enum Ctr {
+    CTR_QUEUE = 0,    // slice queue head (first walk)
+    CTR_QUEUE2 = 1,   // slice queue head (second walk)
+    CTR_COUNT = 2,    // total count
+    CTR_FOUND = 3,    // predicate found flag
+    CTR_MINC = 4,     // UINT32_MAX - min length (atomicMax)
+    CTR_MAX = 5,      // max length (atomicMax)
+    CTR_ERR = 6,      // error flags
+    CTR_TOTAL = 7,    // enumerate: total rows (from the scan)
+    CTR_N = 16
+};
+
+struct Scratch {
+    uint64_t* ctr;        // CTR_N counters
+    uint64_t* W;          // nw * (n + 1) leaf weights
+    int8_t* E;            // lcm
+    int32_t* X0;          // lcm
+    int32_t* YD;          // lcm
+    uint64_t* slice_cnt;  // S
+    uint64_t* slice_off;  // S + 1
+    uint64_t* D;          // dbins (global difference array)
+};
+
+// Predicate constants for the ANY consumer.
+struct PredConst {
+    int64_t w[FS_MAX_D];  // weight of each walk level (0 for virtual levels)
+    int64_t c;
+    int32_t op;
+    int32_t modulus;      // 0: comparison; else congruence
+    // pair: value changes by dw per step t of the pair
+    int64_t dw;
+    // congruence data: g = gcd(dw mod M, M), Mq = M / g, invq = (dw/g)^-1 mod Mq
+    int64_t gM, Mq, invq;
+};
+
+}  // namespace fsi
