@@ -343,6 +343,28 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small case of the same kernels for ncu captures: the config-2
+    generators at a smaller n (output still larger than L2), a few calls."""
+    import torch
+    import paper_2405_07989_gb300 as fs
+    from paper_2405_07989_gb300 import workloads
+    _, g = workloads.CONFIG2
+    n = args.profile_n
+    d = len(g)
+    Z = fs.fs_count(n, g)
+    out = torch.empty(Z * d, dtype=torch.int32, device="cuda")
+    dc = torch.zeros(2, dtype=torch.int64, device="cuda")
+    for _ in range(args.steps):
+        fs.fs_count_async(n, g, dc[0:1])
+        fs.fs_enumerate_async(n, g, out, Z, dc[1:2])
+    torch.cuda.synchronize()
+    assert int(dc[0]) == Z and int(dc[1]) == Z
+    print(json.dumps({"profile_case": {"n": n, "gens": list(g), "rows": Z,
+                                       "bytes": Z * d * 4, "calls": args.steps}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,7 +372,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only a small case of the same kernels (for ncu)")
+    ap.add_argument("--profile-n", type=int, default=2000)
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

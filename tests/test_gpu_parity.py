@@ -306,13 +306,16 @@ def test_plan_and_slice_counts_match_oracle(slices):
                 assert counts[s] == c, (n, g, s)
                 total += c
             assert total == oracle.count_dp(n, g)
-        # bounds are clean prefixes (leaf, 0, 0), strictly increasing, phi <= n
+        # bounds are clean prefixes (leaf, 0, 0) with phi <= n, non-decreasing
+        # (an empty slice repeats the next slice's bound), min(S, L) distinct
         live = [b for b in bounds[:-1] if b[0] >= 0]
         for b in live:
             assert b[-1] == 0 and (len(b) < 3 or b[-2] == 0)
             assert sum(x * y for x, y in zip(b, wg)) <= n
-        assert all(tuple(a) < tuple(b) for a, b in zip(live, live[1:]))
-        assert len(live) == min(slices, leaves)
+        assert all(tuple(a) <= tuple(b) for a, b in zip(live, live[1:]))
+        assert len(set(map(tuple, live))) == min(slices, leaves)
+        if slices <= leaves:
+            assert len(live) == slices
 
 
 def test_enumerate_slices_sampled_against_oracle_stream():
@@ -369,7 +372,7 @@ def test_config2_full():
         key = key * 512 + rows[:, k].to(torch.int64)
     for c0 in range(0, expect, 1 << 24):
         blk = rows[c0:c0 + (1 << 24)].to(torch.int64)
-        assert bool(torch.all(blk @ gv == n))
+        assert bool(torch.all((blk * gv).sum(dim=1) == n))
         assert bool(torch.all(blk >= 0))
     assert bool(torch.all(key[1:] > key[:-1]))
     counts = fs.fs_slice_counts(n, g, S, cfg)
