@@ -206,6 +206,39 @@ void fs_profile_enable(int on);
  * Returns the number of entries (-1 on a CUDA error). */
 int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max);
 
+/* --- allocation-free count ---------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory.  Examples: a framework
+ * that owns all device memory through its own pool or budget, where a
+ * cudaMalloc behind its back can fail or fragment the pool; a latency-critical
+ * serving loop, where cudaMalloc / cudaFree synchronise the device and take
+ * unbounded time; and code that has exhausted its memory quota.
+ *
+ * fs_count_noalloc enqueues the same work as fs_count_async (leaf-count and
+ * pair tables, then the count walk) but takes its scratch from a static
+ * device array of FS_NOALLOC_SCRATCH_BYTES inside the library instead of the
+ * cudaMalloc'd arena.  It calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * other allocating routine.
+ *   dev_count : DEVICE uint64 receiving |Z| in stream order (the caller's memory).
+ *   n, gens, d, stream : as fs_count.
+ * Limits and behaviour:
+ * - a query whose tables need more than FS_NOALLOC_SCRATCH_BYTES
+ *   ((d-3) (n+1) 8 bytes of leaf counts plus up to 16 KB) is rejected with
+ *   FS_E_OVERFLOW and a message naming the size, before any device work;
+ * - the static array costs every device that loads this library
+ *   FS_NOALLOC_SCRATCH_BYTES of memory until the process exits;
+ * - the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture;
+ * - every call on a device shares the one array and each call re-zeroes the
+ *   counters it needs; calls whose work overlaps on the GPU (different
+ *   streams, no ordering between them) race on the array and give wrong
+ *   results: order them on one stream or with events. */
+#define FS_NOALLOC_SCRATCH_BYTES (4u << 20)
+fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, uint64_t* dev_count,
+                           void* stream);
+
 /* --- host-side self test of the division helper ------------------------- */
 
 /* Checks the library's division by an invariant divisor (Granlund-Montgomery

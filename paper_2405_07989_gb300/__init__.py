@@ -80,6 +80,7 @@ SIGNATURES = {
                                _i32p, _i32p, _u64p]),
     "fs_slice_counts": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
                                        ctypes.c_int64, _u64p, _vp]),
+    "fs_count_noalloc": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _vp, _vp]),
     "fs_profile_enable": (None, [ctypes.c_int]),
     "fs_profile_read": (ctypes.c_int, [ctypes.c_char_p, _u64p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int]),
@@ -239,6 +240,13 @@ def fs_slice_counts(n: int, gens, slices: int, cfg: fs_config | None = None, str
     out = (ctypes.c_uint64 * slices)()
     _check(lib().fs_slice_counts(int(n), g, d, _cfgp_of(cfg), int(slices), out, _stream(stream)))
     return [int(x) for x in out]
+
+
+def fs_count_noalloc(n: int, gens, dev_count, stream=None) -> None:
+    """Enqueue the count using the library's static scratch (no allocation);
+    |Z| lands in dev_count[0] (a CUDA 64-bit tensor)."""
+    g, d = _gens(gens)
+    _check(lib().fs_count_noalloc(int(n), g, d, _ptr(dev_count), _stream(stream)))
 
 
 def fs_profile_enable(on: bool = True) -> None:

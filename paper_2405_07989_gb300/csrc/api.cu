@@ -758,3 +758,74 @@ int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count)
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free count (fs_count_noalloc)
+// ===========================================================================
+// Its scratch is the static device array below instead of the cudaMalloc'd
+// arena: every device that loads the library holds FS_NOALLOC_SCRATCH_BYTES
+// of it until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress while that device is current.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+}  // namespace
+
+extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, uint64_t* dev_count,
+                                      void* stream)
+{
+    if (!dev_count) return fail(FS_E_INVAL, "dev_count is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    fs_config cfg = cfg_or_default(nullptr);
+    Query Q;
+    fs_status s = build_query(n, gens, d, cfg, Q);
+    if (s != FS_OK) return s;
+    QueryConst q = Q.q;
+    q.tab_xy = 0;  // the count walk reads only the E table
+    // scratch layout inside the static array: counters | leaf counts W | E table
+    const size_t off_W = al(CTR_N * 8);
+    const size_t off_E = off_W + al((size_t)q.nw * (size_t)(q.n + 1) * 8);
+    const size_t need = off_E + al(q.tab_e ? q.lcm : 0);
+    if (need > (size_t)FS_NOALLOC_SCRATCH_BYTES)
+        return fail(FS_E_OVERFLOW,
+                    "fs_count_noalloc: this query needs %zu bytes of scratch; the static maximum "
+                    "is %zu bytes (FS_NOALLOC_SCRATCH_BYTES); use fs_count",
+                    need, (size_t)FS_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(FS_E_CUDA, "device %d out of range", dev);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_addr[dev] = ptr;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    LaunchCfg lc;
+    s = geometry(q, cfg, OP_COUNT, FS_METHOD_PAIR, 4, sms, lc);
+    if (s != FS_OK) return s;
+    char* base = (char*)g_noalloc_addr[dev];
+    Scratch sc;
+    memset(&sc, 0, sizeof sc);
+    sc.ctr = (uint64_t*)base;
+    sc.W = (uint64_t*)(base + off_W);
+    sc.E = (int8_t*)(base + off_E);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the counters (slice queue head, total) must start at zero on every call
+    e = cudaMemsetAsync(sc.ctr, 0, CTR_N * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = launch_precompute(q, sc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    e = launch_pair(q, sc, OP_COUNT, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "count launch");
+    e = launch_copy_u64(sc.ctr + CTR_COUNT, dev_count, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy launch");
+    return FS_OK;
+}
