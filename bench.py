@@ -314,6 +314,11 @@ def run_gpu(args):
            "d2h_bytes_per_step": Z * row_bytes + 2 * 8 * 16,
            "ms_per_step": e2e_s * 1000.0}
 
+    # ---- extras: the integer-bound count walk on the heavy count-only query ----
+    extras = None
+    if not args.no_extras:
+        extras = heavy_count_extras(fs, workloads, dev)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----
     cpu = None
     if pool is not None:
@@ -335,7 +340,7 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "factorizations_per_step": Z,
                        "output_bytes": alg_bytes, "l2": "flushed between steps (256 MB write)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "breakdown": breakdown,
+            "clocks": clk, "breakdown": breakdown, "extras": extras,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -343,12 +348,87 @@ def run_gpu(args):
     return 0
 
 
+# Integer operations the PAIR count walk spends on one leaf in closed form: residual
+# step, quotient (multiply-high + shift), remainder (multiply-subtract), table
+# load, add, clamp, accumulate.
+COUNT_OPS_PER_LEAF = 8
+
+
+def heavy_count_extras(fs, workloads, dev):
+    """Count and length statistics of the count-only heavy query (8 generators
+    from seed 0, n = 40000, 7.66e12 factorizations), event-timed, with the
+    count walk's integer roofline against the probed add rate."""
+    import torch
+    n, g = workloads.config3(0)
+    rates = {name: fs.fs_probe_int_rate(k, 2048) for k, name in ((0, "add"), (1, "lop3"),
+                                                                  (2, "mad"))}
+    pair = fs.make_config(method=fs.METHOD_PAIR)
+    _, _, leaves = fs.fs_plan(n, g, 1, pair)
+    dc = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def timed_count(cfg, walk):
+        fs.fs_count_async(n, g, dc, cfg)
+        torch.cuda.synchronize()
+        fs.fs_profile_read()
+        fs.fs_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fs.fs_count_async(n, g, dc, cfg)
+        e1.record()
+        torch.cuda.synchronize()
+        fs.fs_profile_enable(False)
+        prof = fs.fs_profile_read()
+        ms = e0.elapsed_time(e1)
+        return int(dc[0].item()), ms, prof.get(walk, (1, ms))[1], prof
+
+    Z, ms, walk_ms, _ = timed_count(pair, "pair_count")
+    Z3, ms3, walk3, prof3 = timed_count(None, "triple_count")
+    assert Z3 == Z
+    achieved = leaves * COUNT_OPS_PER_LEAF / (walk_ms / 1000.0)
+    hist = torch.zeros(n // min(g) + 1, dtype=torch.int64, device=dev)
+    t0 = time.perf_counter()
+    cnt, mn, mx = fs.fs_length_stats(n, g, hist)
+    len_s = time.perf_counter() - t0
+    assert cnt == Z
+    t0 = time.perf_counter()
+    assert fs.fs_length_stats(n, g, None) == (cnt, mn, mx)
+    len_minmax_s = time.perf_counter() - t0
+    return {
+        "workload": f"count-only heavy query g={tuple(g)}, n={n}",
+        "factorizations": Z, "leaves": leaves, "count_ms": ms, "count_walk_ms": walk_ms,
+        "count_factorizations_per_s": Z / (ms / 1000.0), "count_leaves_per_s": leaves / (walk_ms / 1000.0),
+        "count_triple_ms": ms3, "count_triple_walk_ms": walk3,
+        "count_triple_factorizations_per_s": Z / (ms3 / 1000.0),
+        "count_triple_breakdown_ms": {k: v[1] for k, v in prof3.items()},
+        "count_roofline": {"bound": "alu", "achieved": achieved, "peak": rates["add"],
+                           "unit": "int32 lane-ops/s", "frac": achieved / rates["add"],
+                           "ops_per_leaf": COUNT_OPS_PER_LEAF, "peak_source": "probed add rate"},
+        "int_rates": rates,
+        "length_stats_s": len_s, "length_min_max": [mn, mx],
+        "length_factorizations_per_s": Z / len_s,
+        "length_min_max_only_s": len_minmax_s,
+    }
+
+
 def run_profile_case(args):
-    """A small case of the same kernels for ncu captures: the config-2
-    generators at a smaller n (output still larger than L2), a few calls."""
+    """Small cases of the same kernels for ncu captures, a few calls each:
+    "enum": the single-large-query generators at a smaller n (output still
+    larger than L2); "count": the heavy count-only query's generators at a
+    smaller n (same run structure, milliseconds instead of seconds)."""
     import torch
     import paper_2405_07989_gb300 as fs
     from paper_2405_07989_gb300 import workloads
+    if args.profile_case in ("count", "count_triple"):
+        n, g = workloads.config3(0, n=args.profile_n)
+        dc = torch.zeros(1, dtype=torch.int64, device="cuda")
+        cfg = fs.make_config(method=fs.METHOD_PAIR if args.profile_case == "count"
+                             else fs.METHOD_TRIPLE)
+        for _ in range(args.steps):
+            fs.fs_count_async(n, g, dc, cfg)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": {"n": n, "gens": list(g), "count": int(dc[0]),
+                                           "calls": args.steps}}))
+        return 0
     _, g = workloads.CONFIG2
     n = args.profile_n
     d = len(g)
@@ -372,7 +452,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", action="store_true",
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the heavy count-only query measurements")
+    ap.add_argument("--profile-case", choices=["enum", "count", "count_triple"], default=None,
                     help="run only a small case of the same kernels (for ncu)")
     ap.add_argument("--profile-n", type=int, default=2000)
     args = ap.parse_args()

@@ -66,10 +66,22 @@ typedef enum fs_status {
  * Sec. 3.2.4 taken all the way, i.e. jump straight to the first valid value of
  * a_{d-1} and count / list the valid values of (a_{d-1}, a_d) without visiting
  * the invalid candidates between them.  Both give identical results. */
-typedef enum fs_method { FS_METHOD_AUTO = 0, FS_METHOD_PLAIN = 1, FS_METHOD_PAIR = 2 } fs_method;
+typedef enum fs_method {
+    FS_METHOD_AUTO = 0,
+    FS_METHOD_PLAIN = 1,
+    FS_METHOD_PAIR = 2,
+    /* TRIPLE: the paper's dynamic behaviour of Sec. 6.1 for the last three
+     * coordinates: for every residual p <= n, tables hold the number of
+     * factorizations of p over the last three generators and their length
+     * range, so the walk visits only the prefixes of the first d-3
+     * coordinates.  Count and min / max length only (fs_count, fs_length_stats
+     * without a histogram, fs_slice_counts); needs d >= 4.  AUTO uses it for
+     * those when it applies, PAIR otherwise. */
+    FS_METHOD_TRIPLE = 3
+} fs_method;
 
 typedef struct fs_config {
-    int32_t method;        /* fs_method; AUTO = PAIR */
+    int32_t method;        /* fs_method; AUTO = TRIPLE where it applies, else PAIR */
     int32_t keep_order;    /* 1: walk the generators in the caller's order.  0 (default):
                               walk them in descending order, which visits the fewest
                               prefixes; the result is the same set (Z does not depend on
@@ -192,6 +204,58 @@ fs_status fs_plan(int64_t n, const uint32_t* gens, int d, const fs_config* cfg, 
 fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
                           int64_t slices, uint64_t* counts, void* stream);
 
+/* --- batched queries ------------------------------------------------------ */
+
+/* Many (n, g) queries of uneven size in one persistent walk launch.  Each
+ * query is planned like a single call (its own leaf counts and pair tables)
+ * and cut into slices of at most `target` leaves, where target is chosen on
+ * the device from the batch's total so that the batch has about
+ * `cfg->slices` work items (default: 8 per resident warp); persistent warps
+ * pop the items from one device queue, so small and large queries share the
+ * GPU without one launch per query. */
+typedef struct fs_query {
+    int64_t n;
+    int32_t d;
+    uint32_t gens[FS_MAX_D];
+} fs_query;
+
+typedef struct fs_result {
+    uint64_t count;    /* |Z(n, g)| */
+    uint32_t min_len;  /* min / max of sum a_i (FS_BATCH_LENGTHS, count > 0), else 0 */
+    uint32_t max_len;
+    int32_t status;    /* FS_OK, or why this query was rejected (FS_E_INVAL, FS_E_OVERFLOW) */
+    int32_t pad;
+} fs_result;
+
+enum { FS_BATCH_COUNT = 0, FS_BATCH_LENGTHS = 1 };
+
+typedef struct fs_batch fs_batch;  /* opaque; owns its device memory */
+
+/* Validates and plans the queries (host pointer, nq >= 1), allocates the
+ * batch's device memory on the current device and uploads the per-query
+ * constants.  Invalid queries are kept with a non-OK status and skipped.
+ * mode: FS_BATCH_COUNT or FS_BATCH_LENGTHS.  cfg (nullable): block_threads
+ * (<= 256), blocks_per_sm, slices (= work items of the whole batch). */
+fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                          fs_batch** out);
+/* Enqueues one complete evaluation of the batch on `stream` (tables, plan,
+ * walk); nothing is allocated and nothing synchronises, so it can be
+ * repeated or captured into a CUDA graph. */
+fs_status fs_batch_launch(fs_batch* b, void* stream);
+/* Waits for `stream` and copies the results of the last launch into
+ * results (host, nq entries).  FS_E_CUDA if the device reported a fault. */
+fs_status fs_batch_results(fs_batch* b, fs_result* results, void* stream);
+/* Frees the batch (waits for its work to finish). */
+fs_status fs_batch_destroy(fs_batch* b);
+/* create + launch + results + destroy. */
+fs_status fs_batch_run(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                       fs_result* results, void* stream);
+/* Times the batch under a set of launch shapes and work-item counts and
+ * returns the fastest configuration in *best (and its time in *best_ms,
+ * nullable).  Every candidate computes the same exact results. */
+fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config* best,
+                            double* best_ms, void* stream);
+
 /* --- kernel timing ------------------------------------------------------ */
 
 /* While enabled (on != 0), every kernel the library launches is bracketed by
@@ -224,8 +288,9 @@ int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max);
  *   n, gens, d, stream : as fs_count.
  * Limits and behaviour:
  * - a query whose tables need more than FS_NOALLOC_SCRATCH_BYTES
- *   ((d-3) (n+1) 8 bytes of leaf counts plus up to 16 KB) is rejected with
- *   FS_E_OVERFLOW and a message naming the size, before any device work;
+ *   ((d-3) (n+1) 8 bytes of leaf counts, plus up to 16 KB of pair table and
+ *   256 KB of slice start states) is rejected with FS_E_OVERFLOW and a message
+ *   naming the size, before any device work;
  * - the static array costs every device that loads this library
  *   FS_NOALLOC_SCRATCH_BYTES of memory until the process exits;
  * - the first call on a device looks up the array's device address
@@ -238,6 +303,16 @@ int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max);
 #define FS_NOALLOC_SCRATCH_BYTES (4u << 20)
 fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, uint64_t* dev_count,
                            void* stream);
+
+/* --- integer throughput probe ------------------------------------------- */
+
+/* Measures the GPU-wide rate of one 32-bit integer instruction kind (0: add,
+ * 1: three-input logic, 2: multiply-add) with 8 independent chains per
+ * thread on every SM, timed with CUDA events on the legacy default stream:
+ * the denominator of the roofline of the integer-bound walks.  *ops_per_s
+ * (host) receives lane-operations per second.  Returns FS_OK, FS_E_INVAL for a
+ * bad kind, FS_E_CUDA on a CUDA error. */
+fs_status fs_probe_int_rate(int kind, uint32_t iters, double* ops_per_s);
 
 /* --- host-side self test of the division helper ------------------------- */
 

@@ -19,7 +19,7 @@ MAX_D = 16
 
 FS_OK, FS_E_INVAL, FS_E_OVERFLOW, FS_E_CAPACITY = 0, 1, 2, 3
 FS_E_NOMEM, FS_E_CUDA, FS_E_TIMEOUT, FS_E_NOTIMPL = 4, 5, 6, 7
-METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR = 0, 1, 2
+METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR, METHOD_TRIPLE = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -46,6 +46,17 @@ class fs_predicate(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int32 * MAX_D), ("c", ctypes.c_int64), ("op", ctypes.c_int32),
                 ("modulus", ctypes.c_uint32)]
 
+
+class fs_query(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("gens", ctypes.c_uint32 * MAX_D)]
+
+
+class fs_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+BATCH_COUNT, BATCH_LENGTHS = 0, 1
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -81,9 +92,20 @@ SIGNATURES = {
     "fs_slice_counts": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
                                        ctypes.c_int64, _u64p, _vp]),
     "fs_count_noalloc": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _vp, _vp]),
+    "fs_batch_create": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int, _cfgp,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "fs_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "fs_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(fs_result), _vp]),
+    "fs_batch_destroy": (ctypes.c_int, [_vp]),
+    "fs_batch_run": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int, _cfgp,
+                                    ctypes.POINTER(fs_result), _vp]),
+    "fs_batch_autotune": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int,
+                                         _cfgp, ctypes.POINTER(ctypes.c_double), _vp]),
     "fs_profile_enable": (None, [ctypes.c_int]),
     "fs_profile_read": (ctypes.c_int, [ctypes.c_char_p, _u64p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int]),
+    "fs_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_double)]),
     "fs_selftest_division": (ctypes.c_int64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
 }
 
@@ -249,6 +271,77 @@ def fs_count_noalloc(n: int, gens, dev_count, stream=None) -> None:
     _check(lib().fs_count_noalloc(int(n), g, d, _ptr(dev_count), _stream(stream)))
 
 
+def _queries(queries):
+    arr = (fs_query * len(queries))()
+    for i, (n, gens) in enumerate(queries):
+        g = [int(x) for x in gens]
+        arr[i].n = int(n)
+        arr[i].d = len(g)
+        for j, x in enumerate(g[:MAX_D]):
+            arr[i].gens[j] = x & 0xffffffff
+    return arr
+
+
+def _results(res):
+    return [(int(r.count), int(r.min_len), int(r.max_len), int(r.status)) for r in res]
+
+
+def fs_batch_run(queries, mode: int = BATCH_LENGTHS, cfg: fs_config | None = None, stream=None):
+    """[(count, min_len, max_len, status)] for queries = [(n, gens), ...], in one
+    persistent launch."""
+    q = _queries(queries)
+    res = (fs_result * len(queries))()
+    _check(lib().fs_batch_run(q, len(queries), int(mode), _cfgp_of(cfg), res, _stream(stream)))
+    return _results(res)
+
+
+def fs_batch_autotune(queries, mode: int = BATCH_LENGTHS, stream=None):
+    """(fs_config, ms): the fastest launch shape / work-item count for the batch."""
+    q = _queries(queries)
+    best = fs_config()
+    ms = ctypes.c_double(0)
+    _check(lib().fs_batch_autotune(q, len(queries), int(mode), ctypes.byref(best),
+                                   ctypes.byref(ms), _stream(stream)))
+    return best, float(ms.value)
+
+
+class Batch:
+    """A planned batch of queries: launch() enqueues one evaluation (repeatable,
+    capturable in a CUDA graph), results() waits and returns them."""
+
+    def __init__(self, queries, mode: int = BATCH_LENGTHS, cfg: fs_config | None = None):
+        self.n = len(queries)
+        self._q = _queries(queries)
+        h = ctypes.c_void_p(0)
+        _check(lib().fs_batch_create(self._q, self.n, int(mode), _cfgp_of(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().fs_batch_launch(self._h, _stream(stream)))
+
+    def results(self, stream=None):
+        res = (fs_result * self.n)()
+        _check(lib().fs_batch_results(self._h, res, _stream(stream)))
+        return _results(res)
+
+    def close(self):
+        if self._h:
+            lib().fs_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fs_profile_enable(on: bool = True) -> None:
     """Bracket every library kernel launch with CUDA events (for benchmarks)."""
     lib().fs_profile_enable(1 if on else 0)
@@ -267,6 +360,13 @@ def fs_profile_read(max_entries: int = 64):
         nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(ms[i]))
     return out
+
+
+def fs_probe_int_rate(kind: int, iters: int = 4096) -> float:
+    """GPU-wide 32-bit integer lane-ops/s of kind 0 (add), 1 (lop3), 2 (mad)."""
+    out = ctypes.c_double(0)
+    _check(lib().fs_probe_int_rate(int(kind), int(iters), ctypes.byref(out)))
+    return float(out.value)
 
 
 def fs_selftest_division(div: int, x0: int, count: int) -> int:

@@ -275,6 +275,21 @@ int method_of(const fs_config& c)
     return c.method == FS_METHOD_PLAIN ? FS_METHOD_PLAIN : FS_METHOD_PAIR;
 }
 
+// The query the TRIPLE walk runs over: the first D-3 levels as prefix levels
+// (one fewer than PAIR); the last three come from the trailing tables.
+QueryConst reduce_triple(const QueryConst& q)
+{
+    QueryConst r = q;
+    r.D = q.D - 1;
+    r.P = q.P - 1;
+    r.dv_in = q.dv_h[r.P - 1];
+    r.nw = r.P - 1;
+    r.tab_e = 0;
+    r.tab_xy = 0;
+    r.lcm = 0;
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // launch geometry and scratch layout
 // ---------------------------------------------------------------------------
@@ -286,6 +301,11 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
     if (method == FS_METHOD_PLAIN) {
         lc.threads = 128;
         e = plain_occupancy(q, op, lc.threads, &bps);
+    } else if (method == FS_METHOD_TRIPLE) {
+        int t = cfg.block_threads > 0 ? cfg.block_threads : 256;
+        if (t % 32 != 0 || t > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", t);
+        lc.threads = t;
+        e = triple_occupancy(lc.threads, &bps);
     } else {
         int t = cfg.block_threads > 0 ? cfg.block_threads : 256;
         if (t % 32 != 0 || t > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", t);
@@ -296,22 +316,34 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
     if (bps < 1) return fail(FS_E_CUDA, "kernel does not fit on an SM");
     if (cfg.blocks_per_sm > 0) bps = std::min(bps, cfg.blocks_per_sm);
     lc.blocks = sms * bps;
+    // Slice count: explicit, or (auto) as many as leave about MIN_LEAVES leaves
+    // per slice, at most 8 slices per warp (PAIR) / 2 per thread (PLAIN); the
+    // planner picks the final number on the device, where the leaf count is.
+    // Eight slices per warp: the cost of a leaf varies with its run's length
+    // and, for the enumerate walk, with its row count.
     uint64_t S;
-    if (cfg.slices > 0) S = (uint64_t)cfg.slices;
-    else if (method == FS_METHOD_PLAIN) S = (uint64_t)lc.blocks * lc.threads * 2;
-    else S = (uint64_t)lc.blocks * (lc.threads / 32) * 8;
+    if (cfg.slices > 0) {
+        S = (uint64_t)cfg.slices;
+        lc.auto_s = 0;
+    } else {
+        const uint64_t per_warp = 8;
+        S = method == FS_METHOD_PLAIN ? (uint64_t)lc.blocks * lc.threads * 2
+                                      : (uint64_t)lc.blocks * (lc.threads / 32) * per_warp;
+        lc.auto_s = 1;
+    }
+    lc.min_leaves = method == FS_METHOD_PLAIN ? 16 : 256;
     if (S > (1ull << 31)) return fail(FS_E_INVAL, "slices = %llu exceeds 2^31", (unsigned long long)S);
     lc.S = S;
     return FS_OK;
 }
 
 struct Layout {
-    size_t ctr, W, E, X0, YD, cnt, off, D, extra, total;
+    size_t ctr, W, E, X0, YD, cnt, off, D, starts, T3, MN3, MX3, extra, total;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes)
+Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes, bool triple = false)
 {
     Layout L;
     size_t p = 0;
@@ -331,6 +363,15 @@ Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes)
     p = al(p + (size_t)(S + 1) * 8);
     L.D = p;
     p = al(p + (size_t)std::max(q.dbins, q.maxlen + 1) * 8);
+    L.starts = p;
+    p = al(p + (size_t)S * START_W * 4);
+    const size_t tn = triple ? (size_t)q.n + 1 : 0;
+    L.T3 = p;
+    p = al(p + tn * 8);
+    L.MN3 = p;
+    p = al(p + tn * 4);
+    L.MX3 = p;
+    p = al(p + tn * 4);
     L.extra = p;
     p = al(p + extra_bytes);
     L.total = p;
@@ -349,6 +390,7 @@ Scratch scratch_at(void* base, const Layout& L)
     s.slice_cnt = (uint64_t*)(b + L.cnt);
     s.slice_off = (uint64_t*)(b + L.off);
     s.D = (uint64_t*)(b + L.D);
+    s.starts = (int32_t*)(b + L.starts);
     return s;
 }
 
@@ -357,7 +399,8 @@ const char* walk_name(Op op, int method)
     static const char* pair[] = {"pair_count", "pair_slice_count", "pair_len", "pair_any", "pair_enum"};
     static const char* plain[] = {"plain_count", "plain_slice_count", "plain_len", "plain_any",
                                   "plain_enum"};
-    return method == FS_METHOD_PLAIN ? plain[op] : pair[op];
+    static const char* triple[] = {"triple_count", "triple_slice_count", "triple_len", "", ""};
+    return method == FS_METHOD_PLAIN ? plain[op] : method == FS_METHOD_TRIPLE ? triple[op] : pair[op];
 }
 
 cudaError_t launch_walk(const QueryConst& q, const Scratch& sc, Op op, int method, const LaunchCfg& lc,
@@ -372,6 +415,7 @@ cudaError_t launch_walk(const QueryConst& q, const Scratch& sc, Op op, int metho
 // Everything a call enqueues: precompute, walk(s), finalisation.
 struct Call {
     Query Q;
+    QueryConst q3;  // TRIPLE: the reduced query the walk runs over
     fs_config cfg;
     int method = FS_METHOD_PAIR;
     DevState* ds = nullptr;
@@ -379,35 +423,68 @@ struct Call {
     Layout L;
     LaunchCfg lc;
     cudaStream_t st = nullptr;
+    uint64_t* T3 = nullptr;
+    int32_t* MN3 = nullptr;
+    int32_t* MX3 = nullptr;
+    const QueryConst& wq() const { return method == FS_METHOD_TRIPLE ? q3 : Q.q; }
 };
 
+// lengths_only: an OP_LEN call that wants no histogram (TRIPLE can serve it)
 fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_config* cfg, Op op,
-                  int eb, void* stream, size_t extra_bytes = 0)
+                  int eb, void* stream, size_t extra_bytes = 0, bool lengths_only = false)
 {
     c.cfg = cfg_or_default(cfg);
-    c.method = method_of(c.cfg);
     c.st = (cudaStream_t)stream;
     fs_status s = build_query(n, gens, d, c.cfg, c.Q);
     if (s != FS_OK) return s;
+    const bool tri_ok = c.Q.q.D >= 4 && c.Q.q.n < (1 << 27) &&
+                        (op == OP_COUNT || op == OP_SLICES || (op == OP_LEN && lengths_only));
+    if (c.cfg.method == FS_METHOD_PLAIN) {
+        c.method = FS_METHOD_PLAIN;
+    } else if (c.cfg.method == FS_METHOD_TRIPLE) {
+        if (!tri_ok)
+            return fail(FS_E_NOTIMPL, "TRIPLE serves count / slice counts / min-max lengths with "
+                                      "d >= 4 and n < 2^27 only");
+        c.method = FS_METHOD_TRIPLE;
+    } else if (c.cfg.method == FS_METHOD_AUTO && tri_ok) {
+        c.method = FS_METHOD_TRIPLE;
+    } else {
+        c.method = FS_METHOD_PAIR;
+    }
+    const bool triple = c.method == FS_METHOD_TRIPLE;
+    if (triple) c.q3 = reduce_triple(c.Q.q);
+    const QueryConst& qw = c.wq();
     s = get_dev(&c.ds);
     if (s != FS_OK) return s;
     // the enumerate count walk and write walk share the slicing: take the
     // geometry of the write walk for both
-    s = geometry(c.Q.q, c.cfg, op == OP_ENUM && c.method == FS_METHOD_PAIR ? OP_ENUM : op, c.method,
+    s = geometry(qw, c.cfg, op == OP_ENUM && c.method == FS_METHOD_PAIR ? OP_ENUM : op, c.method,
                  eb, c.ds->sms, c.lc);
     if (s != FS_OK) return s;
-    c.L = make_layout(c.Q.q, c.lc.S, extra_bytes);
+    c.L = make_layout(qw, c.lc.S, extra_bytes, triple);
     s = ensure_arena(c.ds, c.L.total);
     if (s != FS_OK) return s;
     c.sc = scratch_at(c.ds->arena, c.L);
+    if (triple) {
+        char* b = (char*)c.ds->arena;
+        c.T3 = (uint64_t*)(b + c.L.T3);
+        c.MN3 = (int32_t*)(b + c.L.MN3);
+        c.MX3 = (int32_t*)(b + c.L.MX3);
+    }
     cudaError_t e = cudaMemsetAsync(c.sc.ctr, 0, CTR_N * 8, c.st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     {
-        const QueryConst& q = c.Q.q;
-        ProfScope ps("precompute", c.st, ((q.tab_e || q.tab_xy) ? 1 : 0) + (q.nw > 0 ? 1 : 0));
-        e = launch_precompute(q, c.sc, c.st);
+        ProfScope ps("precompute", c.st,
+                     ((qw.tab_e || qw.tab_xy) ? 1 : 0) + (qw.nw > 0 ? 1 : 0) + (triple ? 1 : 0));
+        e = launch_precompute(qw, c.sc, c.st);
+        if (e == cudaSuccess && triple) e = launch_triple_tables(c.Q.q, c.T3, c.MN3, c.MX3, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    {
+        ProfScope ps("plan", c.st, 1);
+        e = launch_plan(qw, c.sc, c.lc.S, c.lc.auto_s, c.lc.min_leaves, c.st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     return FS_OK;
 }
 
@@ -423,10 +500,19 @@ fs_status read_ctr(Call& c)
     return FS_OK;
 }
 
+cudaError_t call_walk(Call& c, Op op, int queue, const PredConst* pred, void* out, uint64_t cap,
+                      int eb)
+{
+    if (c.method == FS_METHOD_TRIPLE) {
+        ProfScope ps(walk_name(op, c.method), c.st, 1);
+        return launch_triple(c.q3, c.sc, op, c.lc, queue, c.T3, c.MN3, c.MX3, c.st);
+    }
+    return launch_walk(c.Q.q, c.sc, op, c.method, c.lc, queue, pred, out, cap, eb, c.st);
+}
+
 fs_status do_count(Call& c, uint64_t* dev_count)
 {
-    LaunchCfg lc = c.lc;
-    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_COUNT, c.method, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    cudaError_t e = call_walk(c, OP_COUNT, CTR_QUEUE, nullptr, nullptr, 0, 4);
     if (e != cudaSuccess) return cuda_fail(e, "count launch");
     if (dev_count) {
         ProfScope ps("copy_result", c.st, 1);
@@ -443,7 +529,7 @@ fs_status do_enum(Call& c, void* dev_buf, uint64_t cap, int eb, uint64_t* dev_co
     if (e != cudaSuccess) return cuda_fail(e, "enumerate count launch");
     {
         ProfScope ps("scan_slices", c.st, 1);
-        e = launch_scan_slices(c.sc, c.lc.S, dev_count, c.st);
+        e = launch_scan_slices(c.sc, dev_count, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (cap > 0) {
@@ -530,19 +616,23 @@ fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_co
     if (!out) return fail(FS_E_INVAL, "out is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     Call c;
-    fs_status s = prepare(c, n, gens, d, cfg, OP_LEN, 4, stream);
+    fs_status s = prepare(c, n, gens, d, cfg, OP_LEN, 4, stream, 0, hist_dev == nullptr);
     if (s != FS_OK) return s;
     const QueryConst& q = c.Q.q;
-    cudaError_t e = cudaMemsetAsync(c.sc.D, 0, (size_t)std::max(q.dbins, q.maxlen + 1) * 8, c.st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_walk(q, c.sc, OP_LEN, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
-    if (e != cudaSuccess) return cuda_fail(e, "length launch");
-    const int stride = c.method == FS_METHOD_PLAIN ? 0 : std::abs(q.delta);
-    {
+    cudaError_t e;
+    if (c.method == FS_METHOD_TRIPLE) {
+        e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
+        if (e != cudaSuccess) return cuda_fail(e, "length launch");
+    } else {
+        e = cudaMemsetAsync(c.sc.D, 0, (size_t)std::max(q.dbins, q.maxlen + 1) * 8, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
+        if (e != cudaSuccess) return cuda_fail(e, "length launch");
+        const int stride = c.method == FS_METHOD_PLAIN ? 0 : std::abs(q.delta);
         ProfScope ps("len_finalize", c.st, 1);
         e = launch_len_finalize(q, c.sc, hist_dev, stride, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
     s = read_ctr(c);
     if (s != FS_OK) return s;
     out->count = c.ds->pinned[CTR_COUNT];
@@ -653,30 +743,30 @@ fs_status fs_plan(int64_t n, const uint32_t* gens, int d, const fs_config* cfg, 
     fs_config cc = cfg_or_default(cfg);
     cc.slices = slices;
     Call c;
-    const size_t extra = (size_t)slices * FS_MAX_D * 4;
-    fs_status s = prepare(c, n, gens, d, &cc, OP_SLICES, 4, nullptr, extra);
+    fs_status s = prepare(c, n, gens, d, &cc, OP_SLICES, 4, nullptr);
     if (s != FS_OK) return s;
-    const QueryConst& q = c.Q.q;
-    int32_t* dbounds = (int32_t*)((char*)c.ds->arena + c.L.extra);
-    cudaError_t e = launch_plan_bounds(q, c.sc, (uint64_t)slices, dbounds, c.st);
-    if (e != cudaSuccess) return cuda_fail(e, "plan launch");
-    std::vector<int32_t> hb((size_t)slices * q.D);
-    e = cudaMemcpyAsync(hb.data(), dbounds, hb.size() * 4, cudaMemcpyDeviceToHost, c.st);
+    const QueryConst& q = c.wq();
+    std::vector<int32_t> hs((size_t)slices * START_W);
+    cudaError_t e = cudaMemcpyAsync(hs.data(), c.sc.starts, hs.size() * 4, cudaMemcpyDeviceToHost, c.st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-    if (q.P > 1) {
-        e = cudaMemcpyAsync(c.ds->pinned, c.sc.W + q.n, 8, cudaMemcpyDeviceToHost, c.st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-    }
-    e = cudaStreamSynchronize(c.st);
-    if (e != cudaSuccess) return cuda_fail(e, "plan execution");
-    uint64_t L = q.P == 1 ? (uint64_t)(q.n / q.h[0]) + 1 : c.ds->pinned[0];
-    if (leaves) *leaves = L;
+    s = read_ctr(c);
+    if (s != FS_OK) return s;
+    if (leaves) *leaves = c.ds->pinned[CTR_L];
     const int nr = (int)c.Q.real_levels.size();
     if (order)
         for (int j = 0; j < nr; j++) order[j] = q.col[c.Q.real_levels[j]];
     if (bounds) {
-        for (int64_t sl = 0; sl < slices; sl++)
-            for (int j = 0; j < nr; j++) bounds[sl * d + j] = hb[(size_t)sl * q.D + c.Q.real_levels[j]];
+        for (int64_t sl = 0; sl < slices; sl++) {
+            const int32_t* st = &hs[(size_t)sl * START_W];
+            const bool empty = st[START_W - 1] < 0;
+            for (int j = 0; j < nr; j++) {
+                const int k = c.Q.real_levels[j];
+                int32_t v = 0;
+                if (k < q.P - 1) v = st[k];
+                else if (k == q.P - 1) v = st[START_W - 1];
+                bounds[sl * d + j] = empty ? -1 : v;
+            }
+        }
         for (int j = 0; j < d; j++) bounds[slices * d + j] = -1;
     }
     return FS_OK;
@@ -693,7 +783,7 @@ fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_confi
     Call c;
     fs_status s = prepare(c, n, gens, d, &cc, OP_SLICES, 4, stream);
     if (s != FS_OK) return s;
-    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    cudaError_t e = call_walk(c, OP_SLICES, CTR_QUEUE, nullptr, nullptr, 0, 4);
     if (e != cudaSuccess) return cuda_fail(e, "slice count launch");
     e = cudaMemcpyAsync(counts, c.sc.slice_cnt, (size_t)slices * 8, cudaMemcpyDeviceToHost, c.st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
@@ -743,6 +833,264 @@ int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max)
     return k;
 }
 
+fs_status fs_probe_int_rate(int kind, uint32_t iters, double* ops_per_s)
+{
+    if (kind < 0 || kind > 2 || !ops_per_s || iters == 0) return fail(FS_E_INVAL, "bad probe arguments");
+    std::lock_guard<std::mutex> lk(g_mu);
+    double ms = 0;
+    cudaError_t e = int_probe(kind, iters, ops_per_s, &ms);
+    if (e != cudaSuccess) return cuda_fail(e, "integer probe");
+    return FS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched queries
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct fs_batch {
+    int dev = -1;
+    int nq = 0;
+    int mode = 0;
+    std::vector<int32_t> status;
+    void* mem = nullptr;
+    BatchDev bd;
+    int threads = 256;
+    int blocks = 0;
+    int sms = 0;
+};
+
+namespace {
+
+fs_status batch_shape(fs_batch* b, int threads, int blocks_per_sm, uint64_t items)
+{
+    if (threads <= 0) threads = 256;
+    if (threads % 32 != 0 || threads > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", threads);
+    int bps = 0;
+    cudaError_t e = batch_walk_occupancy(b->mode, threads, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (bps < 1) return fail(FS_E_CUDA, "batch kernel does not fit on an SM");
+    if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
+    b->threads = threads;
+    b->blocks = b->sms * bps;
+    const uint64_t warps = (uint64_t)b->blocks * (threads / 32);
+    uint64_t target = items > 0 ? items : warps * 8;
+    if (target + (uint64_t)b->nq > b->bd.items_cap) target = b->bd.items_cap - (uint64_t)b->nq;
+    if (target < 1) target = 1;
+    b->bd.items_target = target;
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                          fs_batch** out)
+{
+    if (!queries || !out || nq < 1) return fail(FS_E_INVAL, "batch: queries / out NULL or nq < 1");
+    if (mode != FS_BATCH_COUNT && mode != FS_BATCH_LENGTHS) return fail(FS_E_INVAL, "batch mode %d", mode);
+    std::lock_guard<std::mutex> lk(g_mu);
+    fs_config cc = cfg_or_default(cfg);
+    fs_config walk_cfg = cfg_or_default(nullptr);  // descending walk order
+    fs_batch* b = new fs_batch;
+    b->nq = nq;
+    b->mode = mode;
+    b->status.assign(nq, FS_OK);
+    std::vector<BatchQ> hq(nq);
+    size_t arena = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = arena;
+        arena += (bytes + 15) & ~(size_t)15;
+        return (uint64_t)o;
+    };
+    for (int i = 0; i < nq; i++) {
+        BatchQ& B = hq[i];
+        memset(&B, 0, sizeof B);
+        const fs_query& Q = queries[i];
+        Query qq;
+        fs_status s = FS_E_INVAL;
+        if (Q.d >= 1 && Q.d <= FS_MAX_D) s = build_query(Q.n, Q.gens, Q.d, walk_cfg, qq);
+        if (s != FS_OK) {
+            b->status[i] = s;
+            continue;
+        }
+        B.q = qq.q;
+        B.valid = 1;
+        B.off_W = take((size_t)B.q.nw * (size_t)(B.q.n + 1) * 8);
+        B.off_E = take(B.q.tab_e ? B.q.lcm : 0);
+        const bool xy = mode == FS_BATCH_LENGTHS && B.q.tab_xy;
+        B.off_X0 = take(xy ? (size_t)B.q.lcm * 4 : 0);
+        B.off_YD = take(xy ? (size_t)B.q.lcm * 4 : 0);
+    }
+    cudaError_t e = cudaGetDevice(&b->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "no CUDA device");
+    }
+    // items: room for the largest shape the autotuner tries (32 per warp at
+    // the maximum occupancy of 256-thread blocks) or the requested count
+    int bps = 0;
+    batch_walk_occupancy(mode, 256, &bps);
+    const uint64_t max_items = std::max<uint64_t>((uint64_t)std::max(cc.slices, (int64_t)0),
+                                                  (uint64_t)b->sms * std::max(bps, 1) * 8 * 32);
+    b->bd.items_cap = max_items + (uint64_t)nq;
+    const size_t off_qs = 0;
+    const size_t off_res = al(off_qs + sizeof(BatchQ) * (size_t)nq);
+    const size_t off_ctr = al(off_res + sizeof(BatchRes) * (size_t)nq);
+    const size_t off_st = al(off_ctr + BCTR_N * 8);
+    const size_t off_ar = al(off_st + (size_t)b->bd.items_cap * START_W * 4);
+    const size_t total = al(off_ar + arena);
+    e = cudaMalloc(&b->mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(FS_E_NOMEM, "batch cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    }
+    char* base = (char*)b->mem;
+    b->bd.qs = (BatchQ*)(base + off_qs);
+    b->bd.nq = nq;
+    b->bd.mode = mode;
+    b->bd.arena = (unsigned char*)(base + off_ar);
+    b->bd.starts = (int32_t*)(base + off_st);
+    b->bd.ctr = (uint64_t*)(base + off_ctr);
+    b->bd.res = (BatchRes*)(base + off_res);
+    b->bd.min_leaves = 64;
+    e = cudaMemcpy(b->bd.qs, hq.data(), sizeof(BatchQ) * (size_t)nq, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->mem);
+        delete b;
+        return cuda_fail(e, "batch upload");
+    }
+    fs_status s = batch_shape(b, cc.block_threads, cc.blocks_per_sm, (uint64_t)std::max(cc.slices, (int64_t)0));
+    if (s != FS_OK) {
+        cudaFree(b->mem);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return FS_OK;
+}
+
+fs_status fs_batch_launch(fs_batch* b, void* stream)
+{
+    if (!b) return fail(FS_E_INVAL, "batch is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfScope ps("batch", st, 4);
+    cudaError_t e = cudaMemsetAsync(b->bd.ctr, 0, BCTR_N * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->bd.res, 0, sizeof(BatchRes) * (size_t)b->nq, st);
+    if (e == cudaSuccess) e = launch_batch(b->bd, b->threads, b->blocks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return FS_OK;
+}
+
+fs_status fs_batch_results(fs_batch* b, fs_result* results, void* stream)
+{
+    if (!b || !results) return fail(FS_E_INVAL, "batch / results is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<BatchRes> hr(b->nq);
+    uint64_t hc[BCTR_N];
+    cudaError_t e = cudaMemcpyAsync(hr.data(), b->bd.res, sizeof(BatchRes) * (size_t)b->nq,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, b->bd.ctr, sizeof hc, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch execution");
+    if (hc[BCTR_ERR]) return fail(FS_E_CUDA, "internal error in the batch walk (flags %llx)",
+                                  (unsigned long long)hc[BCTR_ERR]);
+    for (int i = 0; i < b->nq; i++) {
+        fs_result& R = results[i];
+        R.count = hr[i].count;
+        R.status = b->status[i];
+        R.pad = 0;
+        if (b->mode == FS_BATCH_LENGTHS && R.count > 0) {
+            R.min_len = (uint32_t)(0xffffffffu - hr[i].minc);
+            R.max_len = (uint32_t)hr[i].max;
+        } else {
+            R.min_len = R.max_len = 0;
+        }
+    }
+    return FS_OK;
+}
+
+fs_status fs_batch_destroy(fs_batch* b)
+{
+    if (!b) return FS_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaError_t e = cudaFree(b->mem);
+    delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "batch free");
+    return FS_OK;
+}
+
+fs_status fs_batch_run(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                       fs_result* results, void* stream)
+{
+    fs_batch* b = nullptr;
+    fs_status s = fs_batch_create(queries, nq, mode, cfg, &b);
+    if (s != FS_OK) return s;
+    s = fs_batch_launch(b, stream);
+    if (s == FS_OK) s = fs_batch_results(b, results, stream);
+    fs_status s2 = fs_batch_destroy(b);
+    return s != FS_OK ? s : s2;
+}
+
+fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config* best,
+                            double* best_ms, void* stream)
+{
+    if (!best) return fail(FS_E_INVAL, "best is NULL");
+    fs_batch* b = nullptr;
+    fs_status s = fs_batch_create(queries, nq, mode, nullptr, &b);
+    if (s != FS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int threads_c[] = {128, 256};
+    const int per_warp_c[] = {2, 8, 32};
+    double best_t = 1e30;
+    fs_config bc;
+    memset(&bc, 0, sizeof bc);
+    for (int t : threads_c)
+        for (int pw : per_warp_c) {
+            {
+                std::lock_guard<std::mutex> lk(g_mu);
+                int bps = 0;
+                batch_walk_occupancy(b->mode, t, &bps);
+                const uint64_t items = (uint64_t)b->sms * std::max(bps, 1) * (t / 32) * pw;
+                s = batch_shape(b, t, 0, items);
+            }
+            if (s != FS_OK) break;
+            s = fs_batch_launch(b, st);  // warm-up
+            if (s != FS_OK) break;
+            cudaEventRecord(e0, st);
+            s = fs_batch_launch(b, st);
+            cudaEventRecord(e1, st);
+            if (s != FS_OK) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e, "autotune timing");
+                break;
+            }
+            if (ms < best_t) {
+                best_t = ms;
+                bc.block_threads = t;
+                bc.slices = (int64_t)b->bd.items_target;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fs_status s2 = fs_batch_destroy(b);
+    if (s != FS_OK) return s;
+    *best = bc;
+    if (best_ms) *best_ms = best_t;
+    return s2;
+}
+
 int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count)
 {
     if (div == 0 || div > 0x7fffffffu) return -1;
@@ -772,6 +1120,8 @@ namespace {
 // name is only a host-side stand-in, so the address is looked up once per
 // device with cudaGetSymbolAddress while that device is current.
 constexpr int NOALLOC_MAX_DEVICES = 64;
+// slices of the allocation-free count: their start states take 64 bytes each
+constexpr uint64_t NOALLOC_SLICES = 4096;
 void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
 }  // namespace
 
@@ -786,10 +1136,12 @@ extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, ui
     if (s != FS_OK) return s;
     QueryConst q = Q.q;
     q.tab_xy = 0;  // the count walk reads only the E table
-    // scratch layout inside the static array: counters | leaf counts W | E table
+    // scratch layout inside the static array: counters | leaf counts W | E table |
+    // slice start states (at most NOALLOC_SLICES slices)
     const size_t off_W = al(CTR_N * 8);
     const size_t off_E = off_W + al((size_t)q.nw * (size_t)(q.n + 1) * 8);
-    const size_t need = off_E + al(q.tab_e ? q.lcm : 0);
+    const size_t off_st = off_E + al(q.tab_e ? q.lcm : 0);
+    const size_t need = off_st + al((size_t)NOALLOC_SLICES * START_W * 4);
     if (need > (size_t)FS_NOALLOC_SCRATCH_BYTES)
         return fail(FS_E_OVERFLOW,
                     "fs_count_noalloc: this query needs %zu bytes of scratch; the static maximum "
@@ -811,18 +1163,22 @@ extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, ui
     LaunchCfg lc;
     s = geometry(q, cfg, OP_COUNT, FS_METHOD_PAIR, 4, sms, lc);
     if (s != FS_OK) return s;
+    if (lc.S > NOALLOC_SLICES) lc.S = NOALLOC_SLICES;
     char* base = (char*)g_noalloc_addr[dev];
     Scratch sc;
     memset(&sc, 0, sizeof sc);
     sc.ctr = (uint64_t*)base;
     sc.W = (uint64_t*)(base + off_W);
     sc.E = (int8_t*)(base + off_E);
+    sc.starts = (int32_t*)(base + off_st);
     cudaStream_t st = (cudaStream_t)stream;
     // the counters (slice queue head, total) must start at zero on every call
     e = cudaMemsetAsync(sc.ctr, 0, CTR_N * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = launch_precompute(q, sc, st);
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
+    e = launch_plan(q, sc, lc.S, lc.auto_s, lc.min_leaves, st);
+    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     e = launch_pair(q, sc, OP_COUNT, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "count launch");
     e = launch_copy_u64(sc.ctr + CTR_COUNT, dev_count, st);

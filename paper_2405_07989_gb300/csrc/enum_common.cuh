@@ -1,0 +1,100 @@
+// Shared pieces of the enumerate write walks (enum.cu, enum_fixed.cu): the
+// bulk-copy helpers and the per-warp double-buffered staging of rows.
+#pragma once
+
+#include "walk.cuh"
+
+namespace fsi {
+
+enum { ENUM_STG_BYTES = 3072, ENUM_MAPCAP = 256, ENUM_BIG = 1 << 26 };
+// per warp: two staging buffers, the row -> lane map, the run prefix of the
+// generic (d > 8) path
+enum { ENUM_WARP_BYTES = 2 * ENUM_STG_BYTES + ENUM_MAPCAP + 2 * FS_MAX_D * 4 };
+
+// --- bulk async copies, shared -> global (PTX cp.async.bulk, bulk groups) ---
+FS_D void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+FS_D void bulk_store(void* gdst, const void* ssrc, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                     (unsigned long long)__cvta_generic_to_global(gdst)),
+                 "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+                 : "memory");
+}
+FS_D void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one group still reading shared memory
+FS_D void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every group complete (writes performed)
+FS_D void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Per-warp staging of consecutive output rows in shared memory, drained by
+// the bulk-copy engine.  The staged rows are the global rows
+// [row_base, row_base + nst); element e of the staged block sits at index
+// phase + e of the current buffer, with phase = (row_base d) mod VEC so that
+// 16-byte boundaries line up with the output's.
+template <typename ELEM>
+struct Stager {
+    static constexpr int VEC = 16 / (int)sizeof(ELEM);
+    static constexpr int STG = ENUM_STG_BYTES / (int)sizeof(ELEM);
+    ELEM* out;
+    uint64_t cap_elems;
+    unsigned char* wbase;  // this warp's two buffers
+    uint64_t row_base;
+    int32_t buf, nst, phase, d;
+
+    FS_D ELEM* stg(int k) const { return (ELEM*)(wbase + k * ENUM_STG_BYTES); }
+    FS_D ELEM* cursor() const { return stg(buf) + phase + nst * d; }
+    FS_D bool fits(int rows) const { return phase + (nst + rows) * d <= STG; }
+
+    FS_D void begin(uint64_t row0)
+    {
+        row_base = row0;
+        nst = 0;
+        phase = (int32_t)((row_base * (uint64_t)d) % VEC);
+    }
+
+    // Write the staged rows out (rows past cap are dropped) and switch buffers.
+    FS_D void flush()
+    {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();  // every lane's staged rows are in place
+        if (nst > 0) {
+            const ELEM* sb = stg(buf);
+            const uint64_t g0 = row_base * (uint64_t)d;
+            const uint64_t N = (uint64_t)nst * (uint64_t)d;
+            const uint64_t gend = (g0 + N < cap_elems) ? g0 + N : cap_elems;
+            if (g0 < gend) {
+                const uint32_t span = (uint32_t)(gend - g0);
+                uint32_t head = (uint32_t)((VEC - g0 % VEC) % VEC);
+                if (head > span) head = span;
+                const uint32_t nv = (span - head) / VEC;
+                const uint32_t tail0 = head + nv * VEC;
+                if ((uint32_t)lane < head) out[g0 + lane] = sb[phase + lane];
+                for (uint32_t i = tail0 + lane; i < span; i += 32) out[g0 + i] = sb[phase + i];
+                if (nv > 0) {
+                    fence_proxy_async_smem();  // staging writes -> visible to the bulk copy
+                    __syncwarp();
+                    if (lane == 0) {
+                        bulk_store(out + g0 + head, sb + phase + head, nv * 16u);
+                        bulk_commit();
+                    }
+                }
+            }
+            buf ^= 1;
+            // the buffer we switch to must no longer be read by its earlier copy
+            if (lane == 0) bulk_wait_read_1();
+            __syncwarp();
+        }
+        row_base += (uint64_t)nst;
+        nst = 0;
+        phase = (int32_t)((row_base * (uint64_t)d) % VEC);
+    }
+
+    FS_D void finish()
+    {
+        if ((threadIdx.x & 31) == 0) bulk_wait_all();
+        __syncwarp();
+    }
+};
+
+}  // namespace fsi

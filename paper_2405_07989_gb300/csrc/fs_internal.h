@@ -30,12 +30,12 @@ namespace fsi {
 // (PLDI 1994), Thm 4.2: if 2^(N+l) <= m*dv <= 2^(N+l) + 2^l then
 // floor(x/dv) = floor(m*x / 2^(N+l)) for all 0 <= x < 2^N.  With N = 31,
 // l = ceil(log2 dv) and m = ceil(2^(31+l) / dv) both inequalities hold and
-// m < 2^32, so one 32x32->64 multiply and one 64-bit shift divide any
-// x < 2^31 exactly.
+// m < 2^32.  Since x < 2^31, floor(m x / 2^(31+l)) = floor(m (2x) / 2^(32+l))
+// = (high word of m * 2x) >> l: a multiply-high and a 32-bit shift.
 // ---------------------------------------------------------------------------
 struct Div32 {
     uint32_t m;
-    uint32_t s;   // 31 + l
+    uint32_t l;   // ceil(log2 dv)
     uint32_t dv;
 };
 
@@ -44,15 +44,19 @@ inline Div32 make_div32(uint32_t dv)
     uint32_t l = 0;
     while (l < 32 && ((uint64_t)1 << l) < dv) l++;
     Div32 r;
-    r.s = 31 + l;
-    r.m = (uint32_t)((((uint64_t)1 << r.s) + dv - 1) / dv);
+    r.l = l;
+    r.m = (uint32_t)((((uint64_t)1 << (31 + l)) + dv - 1) / dv);
     r.dv = dv;
     return r;
 }
 
 FS_HD uint32_t div32(uint32_t x, const Div32& q)
 {
-    return (uint32_t)(((uint64_t)x * q.m) >> q.s);
+#if defined(__CUDA_ARCH__)
+    return __umulhi(x + x, q.m) >> q.l;
+#else
+    return (uint32_t)(((uint64_t)(x + x) * q.m) >> 32) >> q.l;
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -61,6 +65,8 @@ FS_HD uint32_t div32(uint32_t x, const Div32& q)
 // (pair tables) are built on the device from these constants.
 // ---------------------------------------------------------------------------
 enum { TABLE_E_MAX = 16384, TABLE_XY_MAX = 4096 };
+// "no solution" bound of the trailing-three length tables
+enum { TRIPLE_NONE = 1 << 30 };
 
 struct QueryConst {
     int32_t n;            // the element
@@ -98,6 +104,8 @@ enum Ctr {
     CTR_MAX = 5,      // max length (atomicMax)
     CTR_ERR = 6,      // error flags
     CTR_TOTAL = 7,    // enumerate: total rows (from the scan)
+    CTR_SEFF = 8,     // number of slices the planner chose
+    CTR_L = 9,        // number of leaves
     CTR_N = 16
 };
 
@@ -110,6 +118,41 @@ struct Scratch {
     uint64_t* slice_cnt;  // S
     uint64_t* slice_off;  // S + 1
     uint64_t* D;          // dbins (global difference array)
+    int32_t* starts;      // S * FS_MAX_D slice start states (planner output)
+};
+
+// ---------------------------------------------------------------------------
+// Batched queries (batch.cu)
+// ---------------------------------------------------------------------------
+struct BatchQ {
+    QueryConst q;
+    uint64_t off_W, off_E, off_X0, off_YD;  // byte offsets of its tables in the arena
+    uint64_t L;      // leaves (device)
+    uint64_t S;      // slices (device)
+    uint64_t item0;  // first work item (device)
+    int32_t valid;   // 0: invalid query, skipped
+    int32_t pad;
+};
+
+struct BatchRes {
+    unsigned long long count;
+    unsigned long long minc;  // UINT32_MAX - min length (atomicMax)
+    unsigned long long max;
+};
+
+enum BatchCtr { BCTR_QUEUE = 0, BCTR_ITEMS = 1, BCTR_ERR = 2, BCTR_N = 8 };
+
+struct BatchDev {
+    BatchQ* qs;
+    int nq;
+    int mode;               // 0: count; 1: count + min / max length
+    unsigned char* arena;   // per-query tables
+    int32_t* starts;        // items_cap * START_W (slice, query, start state)
+    uint64_t items_cap;
+    uint64_t items_target;
+    uint64_t min_leaves;
+    uint64_t* ctr;          // BCTR_N counters
+    BatchRes* res;          // nq results
 };
 
 // Predicate constants for the ANY consumer.

@@ -12,15 +12,19 @@ enum Op { OP_COUNT = 0, OP_SLICES = 1, OP_LEN = 2, OP_ANY = 3, OP_ENUM = 4 };
 struct LaunchCfg {
     int threads;
     int blocks;
-    uint64_t S;  // slices
+    uint64_t S;           // slices (the maximum, when auto_s)
+    int auto_s;           // 1: the planner picks min(S, ceil(L / min_leaves)) slices
+    uint64_t min_leaves;
 };
 
 // tables.cu
 cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream_t st);
-cudaError_t launch_scan_slices(const Scratch& sc, uint64_t S, uint64_t* dev_count, cudaStream_t st);
+cudaError_t launch_scan_slices(const Scratch& sc, uint64_t* dev_count, cudaStream_t st);
 cudaError_t launch_len_finalize(const QueryConst& q, const Scratch& sc, uint64_t* hist, int s,
                                 cudaStream_t st);
 cudaError_t launch_copy_u64(const uint64_t* src, uint64_t* dst, cudaStream_t st);
+cudaError_t launch_triple_tables(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,
+                                 cudaStream_t st);
 
 // pair.cu  (closed-form pair, warp-cooperative walk)
 int pair_smem_bytes(const QueryConst& q, Op op, int threads, int elem_bytes);
@@ -29,14 +33,40 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
                         int queue, const PredConst* pred, void* out, uint64_t cap_rows,
                         int elem_bytes, cudaStream_t st);
 
+// pair.cu: the TRIPLE walk over the reduced query q3 (OP_COUNT, OP_SLICES,
+// OP_LEN = count + min / max length)
+cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
+cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
+                          int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
+                          cudaStream_t st);
+
+// enum_fixed.cu: the write walk specialised on the number of levels and a
+// caller-order / reversed column order; NULL when the query has neither.
+void* pair_enum_fixed_kernel(const QueryConst& q, int elem_bytes);
+
+// enum.cu  (closed-form pair, enumerate write walk)
+int pair_enum_smem_bytes(const QueryConst& q, int threads, int elem_bytes);
+cudaError_t pair_enum_occupancy(const QueryConst& q, int threads, int elem_bytes, int* blocks_per_sm);
+cudaError_t launch_pair_enum(const QueryConst& q, const Scratch& sc, const LaunchCfg& lc, int queue,
+                             void* out, uint64_t cap_rows, int elem_bytes, cudaStream_t st);
+
 // plain.cu  (Algorithm 3.1 per thread)
 cudaError_t plain_occupancy(const QueryConst& q, Op op, int threads, int* blocks_per_sm);
 cudaError_t launch_plain(const QueryConst& q, const Scratch& sc, Op op, const LaunchCfg& lc,
                          int queue, const PredConst* pred, void* out, uint64_t cap_rows,
                          int elem_bytes, cudaStream_t st);
 
-// plan.cu
-cudaError_t launch_plan_bounds(const QueryConst& q, const Scratch& sc, uint64_t S, int32_t* bounds,
-                               cudaStream_t st);
+// batch.cu
+cudaError_t batch_walk_occupancy(int mode, int threads, int* blocks_per_sm);
+cudaError_t launch_batch(const BatchDev& b, int threads, int blocks, cudaStream_t st);
+
+// probe.cu: integer throughput of kind 0 (add), 1 (lop3), 2 (mad) on the whole GPU
+cudaError_t int_probe(int kind, uint32_t iters, double* ops_per_s, double* ms_out);
+
+// tables.cu: the slice planner.  S_req slices, or with auto_s the number of
+// slices min(S_req, ceil(L / min_leaves)) (at least 1), written to ctr[CTR_SEFF]
+// together with L (ctr[CTR_L]) and every slice's start state (sc.starts).
+cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
+                        uint64_t min_leaves, cudaStream_t st);
 
 }  // namespace fsi

@@ -15,36 +15,17 @@ struct SmemQP {
     Div32 dvh[FS_MAX_D];
 };
 
-// Leaf of lex rank `rank` as a full vector (leaf, 0, 0): binary search per
-// level on the exact leaf counts (see warp_unrank).
+// Slice s's start as a full vector (leaf, 0, 0) from the planner's table.
 template <int MAXD>
-FS_D void unrank_thread(const QueryConst& q, const SmemQP& sq, const uint64_t* W, uint64_t rank,
-                        int32_t (&v)[MAXD])
+FS_D void load_start_thread(const QueryConst& q, const int32_t* starts, uint64_t s,
+                            int32_t (&v)[MAXD])
 {
-    int32_t p = q.n;
-    uint64_t rho = rank;
+    const int32_t* st = starts + s * START_W;
 #pragma unroll
-    for (int k = 0; k < MAXD; k++) v[k] = 0;
-    for (int k = 0; k < q.P - 1; k++) {
-        const uint64_t* Wk = W + (size_t)k * (size_t)(q.n + 1);
-        const int32_t h = sq.h[k];
-        const uint64_t top = Wk[p];
-        const uint64_t target = top - rho;
-        int32_t lo = 0, hi = (int32_t)div32((uint32_t)p, sq.dvh[k]);
-        while (lo < hi) {
-            int32_t mid = lo + (hi - lo + 1) / 2;
-            if (Wk[p - mid * h] >= target) lo = mid;
-            else hi = mid - 1;
-        }
-        rho -= top - Wk[p - lo * h];
-        p -= lo * h;
+    for (int k = 0; k < MAXD; k++) v[k] = (k < q.P - 1) ? st[k] : 0;
 #pragma unroll
-        for (int j = 0; j < MAXD; j++)
-            if (j == k) v[j] = lo;
-    }
-#pragma unroll
-    for (int j = 0; j < MAXD; j++)
-        if (j == q.P - 1) v[j] = (int32_t)rho;
+    for (int k = 0; k < MAXD; k++)
+        if (k == q.P - 1) v[k] = st[START_W - 1];
 }
 
 // One nextCandidate step (Algorithm 3.1, steps 2-12).  Returns false at the
@@ -97,11 +78,11 @@ FS_D bool next_candidate(const QueryConst& q, const SmemQP& sq, int32_t (&a)[MAX
 // Walk one slice; cons.emit(a) is called for every valid candidate in the
 // paper's (lex-decreasing) order.  Returns true if the consumer stopped.
 template <int MAXD, class Cons>
-FS_D bool plain_slice(const QueryConst& q, const SmemQP& sq, const uint64_t* W, uint64_t k0,
+FS_D bool plain_slice(const QueryConst& q, const SmemQP& sq, const int32_t* starts, uint64_t s,
                       uint64_t k1, uint64_t L, Cons& cons)
 {
     int32_t lo[MAXD], a[MAXD];
-    unrank_thread<MAXD>(q, sq, W, k0, lo);
+    load_start_thread<MAXD>(q, starts, s, lo);
     bool valid = false;
     if (k1 == L) {
         // the first candidate (x, 0, .., 0), x = ceil(n / g_1)  (Sec. 3.2.1)
@@ -115,7 +96,7 @@ FS_D bool plain_slice(const QueryConst& q, const SmemQP& sq, const uint64_t* W, 
         if (valid && cons.emit(q, sq, a)) return true;
     } else {
         // start at the next slice's lower bound (not part of this slice)
-        unrank_thread<MAXD>(q, sq, W, k1, a);
+        load_start_thread<MAXD>(q, starts, s + 1, a);
     }
     while (next_candidate<MAXD>(q, sq, a, lo, valid)) {
         if (valid && cons.emit(q, sq, a)) return true;
@@ -125,18 +106,22 @@ FS_D bool plain_slice(const QueryConst& q, const SmemQP& sq, const uint64_t* W, 
 }
 
 template <int MAXD, class Cons>
-FS_D void plain_queue(const QueryConst& q, const SmemQP& sq, const Scratch& sc, uint64_t S,
-                      int queue, Cons& cons)
+FS_D void plain_queue(const QueryConst& q, const SmemQP& sq, const Scratch& sc, int queue,
+                      Cons& cons)
 {
-    const uint64_t L = total_leaves(q, sc.W);
+    const uint64_t S = sc.ctr[CTR_SEFF];
+    const uint64_t L = sc.ctr[CTR_L];
+    const SliceSplit split(L, S);
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
-    for (;;) {
-        const unsigned long long s = atomicAdd(qc, 1ull);
+    // thread t takes slice t first, then pops T, T+1, ... from the queue
+    unsigned long long s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (;; s = atomicAdd(qc, 1ull) + T) {
         if (s >= S) break;
-        const uint64_t k0 = slice_start(s, L, S), k1 = slice_start(s + 1, L, S);
+        const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
         cons.slice_begin(sc, s);
         bool stop = false;
-        if (k1 > k0) stop = plain_slice<MAXD>(q, sq, sc.W, k0, k1, L, cons);
+        if (k1 > k0) stop = plain_slice<MAXD>(q, sq, sc.starts, s, k1, L, cons);
         cons.slice_end(sc, s);
         if (stop) break;
     }
@@ -263,7 +248,7 @@ struct PEnum {
 // ---------------------------------------------------------------------------
 template <int MAXD, bool PER_SLICE>
 __global__ void __launch_bounds__(128) k_plain_count(const __grid_constant__ QueryConst q,
-                                                     Scratch sc, uint64_t S, int queue)
+                                                     Scratch sc, int queue)
 {
     __shared__ SmemQP sq;
     __shared__ unsigned long long bsum;
@@ -271,7 +256,7 @@ __global__ void __launch_bounds__(128) k_plain_count(const __grid_constant__ Que
     if (threadIdx.x == 0) bsum = 0;
     __syncthreads();
     PCount c{0, 0, PER_SLICE};
-    plain_queue<MAXD>(q, sq, sc, S, queue, c);
+    plain_queue<MAXD>(q, sq, sc, queue, c);
     uint64_t v = warp_sum_u64(c.total);
     if ((threadIdx.x & 31) == 0) atomicAdd(&bsum, (unsigned long long)v);
     __syncthreads();
@@ -280,7 +265,7 @@ __global__ void __launch_bounds__(128) k_plain_count(const __grid_constant__ Que
 
 template <int MAXD, bool SMEMH>
 __global__ void __launch_bounds__(128) k_plain_len(const __grid_constant__ QueryConst q,
-                                                   Scratch sc, uint64_t S, int queue)
+                                                   Scratch sc, int queue)
 {
     __shared__ SmemQP sq;
     __shared__ unsigned long long bsum;
@@ -300,7 +285,7 @@ __global__ void __launch_bounds__(128) k_plain_len(const __grid_constant__ Query
     }
     __syncthreads();
     PLen c{H, 0, 0xffffffffu, 0};
-    plain_queue<MAXD>(q, sq, sc, S, queue, c);
+    plain_queue<MAXD>(q, sq, sc, queue, c);
     uint64_t v = warp_sum_u64(c.cnt);
     uint32_t mn = c.mn, mx = c.mx;
     for (int o = 16; o > 0; o >>= 1) {
@@ -325,7 +310,7 @@ __global__ void __launch_bounds__(128) k_plain_len(const __grid_constant__ Query
 
 template <int MAXD>
 __global__ void __launch_bounds__(128) k_plain_any(const __grid_constant__ QueryConst q,
-                                                   Scratch sc, uint64_t S, int queue,
+                                                   Scratch sc, int queue,
                                                    const __grid_constant__ PredConst pred)
 {
     __shared__ SmemQP sq;
@@ -334,19 +319,19 @@ __global__ void __launch_bounds__(128) k_plain_any(const __grid_constant__ Query
     if (threadIdx.x == 0) spc = pred;
     __syncthreads();
     PAny c{&spc, (unsigned long long*)&sc.ctr[CTR_FOUND], 0};
-    plain_queue<MAXD>(q, sq, sc, S, queue, c);
+    plain_queue<MAXD>(q, sq, sc, queue, c);
 }
 
 template <int MAXD, typename ELEM>
 __global__ void __launch_bounds__(128) k_plain_enum(const __grid_constant__ QueryConst q,
-                                                    Scratch sc, uint64_t S, int queue, ELEM* out,
+                                                    Scratch sc, int queue, ELEM* out,
                                                     uint64_t cap_rows)
 {
     __shared__ SmemQP sq;
     load_sqp(q, sq);
     __syncthreads();
     PEnum<ELEM> c{out, cap_rows, 0};
-    plain_queue<MAXD>(q, sq, sc, S, queue, c);
+    plain_queue<MAXD>(q, sq, sc, queue, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -377,22 +362,21 @@ static cudaError_t launch_plain_t(const QueryConst& q, const Scratch& sc, Op op,
 {
     const dim3 g(lc.blocks), b(lc.threads);
     const int smem = plain_smem(q, op);
-    const uint64_t S = lc.S;
-    switch (op) {
+        switch (op) {
     case OP_COUNT:
-        return go(k_plain_count<MAXD, false>, g, b, 0, st, q, sc, S, queue);
+        return go(k_plain_count<MAXD, false>, g, b, 0, st, q, sc, queue);
     case OP_SLICES:
-        return go(k_plain_count<MAXD, true>, g, b, 0, st, q, sc, S, queue);
+        return go(k_plain_count<MAXD, true>, g, b, 0, st, q, sc, queue);
     case OP_LEN:
-        return smem ? go(k_plain_len<MAXD, true>, g, b, smem, st, q, sc, S, queue)
-                    : go(k_plain_len<MAXD, false>, g, b, 0, st, q, sc, S, queue);
+        return smem ? go(k_plain_len<MAXD, true>, g, b, smem, st, q, sc, queue)
+                    : go(k_plain_len<MAXD, false>, g, b, 0, st, q, sc, queue);
     case OP_ANY:
-        return go(k_plain_any<MAXD>, g, b, 0, st, q, sc, S, queue, *pred);
+        return go(k_plain_any<MAXD>, g, b, 0, st, q, sc, queue, *pred);
     case OP_ENUM:
         if (elem_bytes == 2)
-            return go(k_plain_enum<MAXD, int16_t>, g, b, 0, st, q, sc, S, queue, (int16_t*)out,
+            return go(k_plain_enum<MAXD, int16_t>, g, b, 0, st, q, sc, queue, (int16_t*)out,
                       cap_rows);
-        return go(k_plain_enum<MAXD, int32_t>, g, b, 0, st, q, sc, S, queue, (int32_t*)out,
+        return go(k_plain_enum<MAXD, int32_t>, g, b, 0, st, q, sc, queue, (int32_t*)out,
                   cap_rows);
     }
     return cudaErrorInvalidValue;
@@ -413,39 +397,6 @@ cudaError_t plain_occupancy(const QueryConst& q, Op op, int threads, int* nb)
     if (q.D <= 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<4, true>, threads, smem);
     if (q.D <= 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<8, true>, threads, smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<16, true>, threads, smem);
-}
-
-// ---------------------------------------------------------------------------
-// planner output: the first leaf of every slice as a full vector (leaf, 0, 0)
-// ---------------------------------------------------------------------------
-__global__ void k_plan_bounds(const __grid_constant__ QueryConst q, Scratch sc, uint64_t S,
-                              int32_t* bounds)
-{
-    __shared__ SmemQP sq;
-    load_sqp(q, sq);
-    __syncthreads();
-    const uint64_t L = total_leaves(q, sc.W);
-    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S;
-         s += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k0 = slice_start(s, L, S);
-        int32_t v[FS_MAX_D];
-        if (k0 < L) {
-            unrank_thread<FS_MAX_D>(q, sq, sc.W, k0, v);
-        } else {
-#pragma unroll
-            for (int k = 0; k < FS_MAX_D; k++) v[k] = -1;
-        }
-        for (int k = 0; k < q.D; k++) bounds[s * q.D + k] = v[k];
-    }
-}
-
-cudaError_t launch_plan_bounds(const QueryConst& q, const Scratch& sc, uint64_t S, int32_t* bounds,
-                               cudaStream_t st)
-{
-    int blocks = (int)((S + 127) / 128);
-    if (blocks > 4096) blocks = 4096;
-    k_plan_bounds<<<blocks, 128, 0, st>>>(q, sc, S, bounds);
-    return cudaGetLastError();
 }
 
 }  // namespace fsi

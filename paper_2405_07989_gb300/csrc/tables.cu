@@ -4,6 +4,7 @@
 //                 (closed form of the congruence step, Sec. 3.2.4)
 //  k_weights      the exact leaf counts W_k[p] that the slice planner unranks
 //                 (balanced division of labour, Sec. 4.1 and Sec. 6.2)
+//  k_plan         the slice planner: slice count and each slice's start state
 //  k_scan_slices  exclusive scan of per-slice counts -> output offsets
 //  k_len_finalize histogram from the strided difference array
 #include "launch.h"
@@ -16,23 +17,7 @@ namespace fsi {
 __global__ void k_pair_tables(const __grid_constant__ QueryConst q, int8_t* E, int32_t* X0,
                               int32_t* YD)
 {
-    const uint32_t lcm = q.lcm;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < lcm;
-         w += gridDim.x * blockDim.x) {
-        int8_t e = -1;
-        int32_t x0 = -1, yd = 0;
-        if (w % (uint32_t)q.G == 0) {
-            uint64_t wg = w / (uint32_t)q.G;
-            uint64_t x = ((wg % (uint64_t)q.v) * (uint64_t)q.inv) % (uint64_t)q.v;
-            int64_t rest = (int64_t)w - (int64_t)x * q.A;  // divisible by B
-            x0 = (int32_t)x;
-            yd = (int32_t)(rest / q.B);
-            e = rest >= 0 ? 1 : 0;
-        }
-        if (E) E[w] = e;
-        if (X0) X0[w] = x0;
-        if (YD) YD[w] = yd;
-    }
+    pair_tables_fill(q, E, X0, YD, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // W_k[p] = #{(a_k..a_{P-1}) >= 0 : sum_{i >= k} a_i h_i <= p} for k = 0..P-2,
@@ -49,18 +34,63 @@ __global__ void __launch_bounds__(1024) k_weights(const __grid_constant__ QueryC
     }
 }
 
-// off[s] = sum_{j < s} cnt[j] for s = 0..S, total -> ctr[CTR_TOTAL] and
-// (optionally) *dev_count.  One block.
+// The slice planner (Sec. 4, the role of Algorithm 4.1): S_req slices, or with
+// auto_s as many as keep about min_leaves leaves per slice (at most S_req);
+// writes the count and every slice's start (its first leaf, found by
+// warp_unrank on the exact leaf counts).  One warp per slice.
+__global__ void __launch_bounds__(256) k_plan(const __grid_constant__ QueryConst q, Scratch sc,
+                                              uint64_t S_req, int auto_s, uint64_t min_leaves)
+{
+    __shared__ int32_t hs[FS_MAX_D];
+    __shared__ Div32 dvh[FS_MAX_D];
+    if (threadIdx.x < FS_MAX_D) {
+        hs[threadIdx.x] = q.h[threadIdx.x];
+        dvh[threadIdx.x] = q.dv_h[threadIdx.x];
+    }
+    __syncthreads();
+    const uint64_t L = total_leaves(q, sc.W);
+    uint64_t S = S_req;
+    if (auto_s) {
+        uint64_t want = (L + min_leaves - 1) / min_leaves;
+        if (want < 1) want = 1;
+        if (want < S) S = want;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc.ctr[CTR_SEFF] = S;
+        sc.ctr[CTR_L] = L;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const SliceSplit split(L, S);
+    for (uint64_t s = gw; s < S; s += nw) {
+        int32_t* st = sc.starts + s * START_W;
+        const uint64_t k0 = split.start(s);
+        if (k0 >= L) {
+            if (lane == 0) st[START_W - 1] = -1;
+            continue;
+        }
+        RunPrefix rp;
+        const int32_t b = warp_unrank(q, hs, dvh, sc.W, k0, lane, rp);
+        if (lane < q.P - 1) st[lane] = rp.a;
+        if (lane == 0) st[START_W - 1] = b;
+    }
+}
+
+// off[s] = sum_{j < s} cnt[j] for s = 0..S (S = the planner's slice count),
+// total -> ctr[CTR_TOTAL] and (optionally) *dev_count.  One block; each thread
+// sums a contiguous run of slices, then a block scan of the runs.
 __global__ void __launch_bounds__(1024) k_scan_slices(const uint64_t* cnt, uint64_t* off,
-                                                      uint64_t S, uint64_t* ctr,
-                                                      uint64_t* dev_count)
+                                                      uint64_t* ctr, uint64_t* dev_count)
 {
     __shared__ uint64_t part[1024];
+    const uint64_t S = ctr[CTR_SEFF];
     const int T = blockDim.x, tid = threadIdx.x;
     const uint64_t per = (S + T - 1) / T;
     const uint64_t b = (uint64_t)tid * per;
     const uint64_t e = b + per < S ? b + per : S;
     uint64_t s = 0;
+#pragma unroll 8
     for (uint64_t i = b; i < e; i++) s += cnt[i];
     part[tid] = s;
     __syncthreads();
@@ -97,6 +127,55 @@ __global__ void __launch_bounds__(1024) k_len_finalize(const __grid_constant__ Q
 
 __global__ void k_copy_u64(const uint64_t* src, uint64_t* dst) { *dst = *src; }
 
+// Trailing-three tables (Sec. 6.1: keep the factorizations of every small
+// residual over the trailing generators, here their count and length range).
+// With h = h_{P-1} and the pair (A, B) of q, for p = 0..n:
+//   T3[p]  = #{(a, x, y) >= 0 : a h + x A + y B = p} = sum_{a >= 0} c2(p - a h)
+//   MN3[p] = min of a + x + y over those solutions (TRIPLE_NONE if none)
+//   MX3[p] = max of a + x + y (-TRIPLE_NONE if none)
+// c2 and the pair's length range come from the pair's closed form (its lengths
+// run l0 + t delta); the sums over a are strided scans: a running sum, and a
+// running min / max of (pair bound - floor(p/h)) plus floor(p/h).  One block.
+__global__ void __launch_bounds__(1024) k_triple_tables(const __grid_constant__ QueryConst q,
+                                                        uint64_t* T3, int32_t* MN3, int32_t* MX3)
+{
+    __shared__ uint64_t part64[1024];
+    __shared__ int32_t part32[1024];
+    const int len = q.n + 1;
+    const int h = q.h[q.P - 1];
+    const Div32 dvh = q.dv_h[q.P - 1];
+    for (int p = threadIdx.x; p < len; p += blockDim.x) {
+        int32_t x0 = 0, y0 = 0;
+        const uint32_t c = pair_xy<false>(q, nullptr, nullptr, p, x0, y0);
+        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
+        T3[p] = c;
+        if (c > 0) {
+            const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
+            MN3[p] = min(l0, l1) - t;
+            MX3[p] = max(l0, l1) - t;
+        } else {
+            MN3[p] = TRIPLE_NONE - t;
+            MX3[p] = -TRIPLE_NONE - t;
+        }
+    }
+    __syncthreads();
+    block_strided_scan<uint64_t>(T3, len, h, part64, (uint64_t)0, OpAdd());
+    block_strided_scan<int32_t>(MN3, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
+    block_strided_scan<int32_t>(MX3, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+    for (int p = threadIdx.x; p < len; p += blockDim.x) {
+        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
+        MN3[p] += t;
+        MX3[p] += t;
+    }
+}
+
+cudaError_t launch_triple_tables(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,
+                                 cudaStream_t st)
+{
+    k_triple_tables<<<1, 1024, 0, st>>>(q, T3, MN3, MX3);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -114,9 +193,19 @@ cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_slices(const Scratch& sc, uint64_t S, uint64_t* dev_count, cudaStream_t st)
+cudaError_t launch_scan_slices(const Scratch& sc, uint64_t* dev_count, cudaStream_t st)
 {
-    k_scan_slices<<<1, 1024, 0, st>>>(sc.slice_cnt, sc.slice_off, S, sc.ctr, dev_count);
+    k_scan_slices<<<1, 1024, 0, st>>>(sc.slice_cnt, sc.slice_off, sc.ctr, dev_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
+                        uint64_t min_leaves, cudaStream_t st)
+{
+    uint64_t blocks = (S_req + 7) / 8;  // one warp per slice
+    if (blocks > 16384) blocks = 16384;
+    if (blocks < 1) blocks = 1;
+    k_plan<<<(unsigned)blocks, 256, 0, st>>>(q, sc, S_req, auto_s, min_leaves);
     return cudaGetLastError();
 }
 

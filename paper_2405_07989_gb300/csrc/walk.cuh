@@ -19,13 +19,18 @@ namespace fsi {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// Slices: slice s holds the leaf ranks [floor(s L / S), floor((s+1) L / S)).
-// Written as s*Q + floor(s*R / S) with L = Q*S + R, exact for S < 2^32.
+// Slices: with L = Q S + R (0 <= R < S), slice s holds the leaf ranks
+// [s Q + min(s, R), (s+1) Q + min(s+1, R)): the first R slices one leaf more.
 // ---------------------------------------------------------------------------
+struct SliceSplit {
+    uint64_t Q, R;
+    FS_HD SliceSplit(uint64_t L, uint64_t S) : Q(L / S), R(L % S) {}
+    FS_HD uint64_t start(uint64_t s) const { return s * Q + (s < R ? s : R); }
+};
+
 FS_HD uint64_t slice_start(uint64_t s, uint64_t L, uint64_t S)
 {
-    uint64_t Q = L / S, R = L % S;
-    return s * Q + (s * R) / S;
+    return SliceSplit(L, S).start(s);
 }
 
 // Number of leaves: W_0[n], or for a single prefix level floor(n / h_0) + 1.
@@ -100,6 +105,71 @@ FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint6
             out[p] = run;
         }
     }
+    __syncthreads();
+}
+
+// Block-wide strided inclusive scan in place: x[p] = op(x[p - s], x[p]) for
+// p = s..len-1, i.e. a running op along each residue class mod s (the same
+// segmented scheme as block_strided_prefix_sum, for any associative op).
+struct OpMin {
+    template <class T>
+    FS_D T operator()(T a, T b) const { return a < b ? a : b; }
+};
+struct OpMax {
+    template <class T>
+    FS_D T operator()(T a, T b) const { return a > b ? a : b; }
+};
+struct OpAdd {
+    template <class T>
+    FS_D T operator()(T a, T b) const { return a + b; }
+};
+
+template <class T, class Op>
+FS_D void block_strided_scan(T* x, int len, int s, T* part, T ident, Op op)
+{
+    const int NT = blockDim.x, tid = threadIdx.x;
+    if (len <= 0) return;
+    if (s >= NT || s >= len) {
+        const int nch = s < len ? s : len;
+        for (int rho = tid; rho < nch; rho += NT) {
+            T acc = ident;
+            for (int p = rho; p < len; p += s) {
+                acc = op(acc, x[p]);
+                x[p] = acc;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    const int G = NT / s;
+    const int cl_max = (len - 1) / s + 1;
+    const int seg = (cl_max + G - 1) / G;
+    const int rho = tid % s, g = tid / s;
+    const bool act = g < G;
+    const int t0 = g * seg, t1 = t0 + seg;
+    T acc = ident;
+    if (act)
+        for (int t = t0; t < t1; t++) {
+            const long long p = rho + (long long)t * s;
+            if (p >= len) break;
+            acc = op(acc, x[p]);
+        }
+    part[tid] = act ? acc : ident;
+    __syncthreads();
+    for (int off = s; off < G * s; off <<= 1) {
+        const T v = (act && tid >= off) ? part[tid - off] : ident;
+        __syncthreads();
+        if (act) part[tid] = op(v, part[tid]);
+        __syncthreads();
+    }
+    T run = (act && g > 0) ? part[tid - s] : ident;
+    if (act)
+        for (int t = t0; t < t1; t++) {
+            const long long p = rho + (long long)t * s;
+            if (p >= len) break;
+            run = op(run, x[p]);
+            x[p] = run;
+        }
     __syncthreads();
 }
 
@@ -186,116 +256,189 @@ FS_D bool warp_next_run(const QueryConst& q, int lane, int32_t hk, RunPrefix& rp
 }
 
 // ---------------------------------------------------------------------------
-// The slice walk.  Cons must provide
-//   void run_loaded(const QueryConst&, int slot, const RunPrefix&, int lane)
-//       -- a run's prefix was loaded into slot 0/1 (warp-uniform call);
+// Slice start states, written once per call by the planner (k_plan): per slice
+// START_W int32, [k] = a_k of the run prefix (k < P-1) and [START_W-1] = the
+// index of the slice's first leaf inside its run (-1 for an empty slice).
+// ---------------------------------------------------------------------------
+constexpr int START_W = FS_MAX_D;
+
+// Loads slice s's start into the lane-distributed run prefix; returns the
+// index of the first leaf inside its run.
+FS_D int32_t warp_load_start(const QueryConst& q, const int32_t* hs, const int32_t* starts,
+                             uint64_t s, int lane, RunPrefix& rp)
+{
+    const int np = q.P - 1;
+    const int32_t* st = starts + s * START_W;
+    const int32_t a = lane < np ? st[lane] : 0;
+    const int32_t b = st[START_W - 1];
+    int32_t ph = lane < np ? a * hs[lane] : 0;
+    int32_t pl = a;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int32_t t1 = __shfl_up_sync(FULL, ph, o);
+        const int32_t t2 = __shfl_up_sync(FULL, pl, o);
+        if (lane >= o) {
+            ph += t1;
+            pl += t2;
+        }
+    }
+    rp.a = a;
+    rp.r = q.n - ph;
+    rp.l = pl;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// The slice walk: the slice's leaves in lex order, run by run.  Within a run
+// (fixed prefix of levels 0..P-2, residual R) the leaves are a_{P-1} = b, b+1,
+// ..., and lane l of a 32-leaf step takes a_{P-1} = b + 32 i + l, residual
+// R - a_{P-1} h_{P-1}; the last step of a run is masked.  Runs that differ only
+// in level P-2 ("siblings") are taken 32 at a time: lane j holds the residual
+// of sibling j, so the lex successor (a ballot over the levels) runs once per
+// group of siblings instead of once per run.  Cons must provide
+//   static constexpr int UNROLL   -- full 32-leaf steps per loop trip
+//   void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)
+//       -- a new run starts (warp-uniform); its prefix is rp.a on lanes
+//          0..P-3 and a2 at level P-2 (rp.a of lane P-2 is stale);
 //   bool chunk(const QueryConst&, int lane, bool valid, int32_t r, int32_t a,
-//              int32_t lp, int slot)
+//              int32_t lp)
 //       -- one leaf per lane: residual r left for the pair, a = a_{P-1},
-//          lp = length of the run prefix, slot of its run; returns true to
-//          stop the walk (warp-uniform).
+//          lp = sum of the run prefix; invalid lanes must not use r; returns
+//          true to stop the walk (warp-uniform);
+//   void fault() -- the slice ran past the last leaf (a planner fault).
 // Returns true if the consumer stopped the walk.
 // ---------------------------------------------------------------------------
 template <class Cons>
-FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh, const uint64_t* W,
-                     uint64_t rank0, uint64_t nleaves, int lane, int32_t hk, Cons& cons)
+FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                     const int32_t* starts, uint64_t s, uint64_t nleaves, int lane, int32_t hk,
+                     Cons& cons)
 {
     RunPrefix rp;
-    int32_t b = warp_unrank(q, hs, dvh, W, rank0, lane, rp);
+    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
     const int np = q.P - 1;
-    const int32_t hin = hs[q.P - 1];
-    int32_t Rc = np > 0 ? __shfl_sync(FULL, rp.r, np - 1) : q.n;
-    int32_t lpc = np > 0 ? __shfl_sync(FULL, rp.l, np - 1) : 0;
-    int32_t lenc = (int32_t)div32((uint32_t)Rc, q.dv_in) + 1;
-    int cs = 0;
-    cons.run_loaded(q, 0, rp, lane);
-    int32_t Rn = -1, lpn = 0, lenn = 0;
-    if (warp_next_run(q, lane, hk, rp)) {
-        Rn = __shfl_sync(FULL, rp.r, np - 1);
-        lpn = __shfl_sync(FULL, rp.l, np - 1);
-        lenn = (int32_t)div32((uint32_t)Rn, q.dv_in) + 1;
-        cons.run_loaded(q, 1, rp, lane);
-    }
+    const uint32_t hin = (uint32_t)hs[np];
+    const uint32_t step = 32u * hin;
     uint64_t rem = nleaves;
     for (;;) {
-        // fast path: whole chunks inside the current run
-        {
-            int32_t k = lenc - b;
-            uint64_t nfull = (uint64_t)(k >> 5);
-            if (rem >> 5 < nfull) nfull = rem >> 5;
-            if (nfull > 0) {
-                int32_t a = b + lane;
-                int32_t r = Rc - a * hin;
-                const int32_t step = 32 * hin;
-                for (uint64_t i = 0; i < nfull; i++) {
-                    if (cons.chunk(q, lane, true, r, a, lpc, cs)) return true;
-                    r -= step;
-                    a += 32;
+        // the current run (prefix of levels 0..P-2) and its siblings
+        int32_t Rc = q.n, lpc = 0, ac = 0;
+        uint32_t hsib = 0, nsib = 1;
+        if (np > 0) {
+            Rc = __shfl_sync(FULL, rp.r, np - 1);
+            lpc = __shfl_sync(FULL, rp.l, np - 1);
+            ac = __shfl_sync(FULL, rp.a, np - 1);
+            hsib = (uint32_t)hs[np - 1];
+            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            if (nsib > 32) nsib = 32;
+        }
+        const int32_t Rj = (int32_t)((uint32_t)Rc - (uint32_t)lane * hsib);
+        for (uint32_t j = 0; j < nsib; j++) {
+            const int32_t R = __shfl_sync(FULL, Rj, (int)j);
+            const int32_t lp = lpc + (int32_t)j;
+            cons.run_begin(q, rp, lane, ac + (int32_t)j);
+            const uint32_t len = div32((uint32_t)R, q.dv_in) + 1;
+            const uint32_t left = len - (uint32_t)b;
+            const uint32_t nh = rem < (uint64_t)left ? (uint32_t)rem : left;
+            // wrap-around arithmetic: lanes past the run end get a meaningless
+            // r and are masked
+            uint32_t a = (uint32_t)b + (uint32_t)lane;
+            uint32_t r = (uint32_t)R - a * hin;
+            const uint32_t full = nh >> 5;  // steps with every lane in the run
+            uint32_t i = 0;
+            if (Cons::UNROLL > 1) {
+                for (; i + Cons::UNROLL <= full; i += Cons::UNROLL) {
+#pragma unroll
+                    for (int u = 0; u < Cons::UNROLL; u++) {
+                        if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                        r -= step;
+                        a += 32;
+                    }
                 }
-                b += (int32_t)(nfull << 5);
-                rem -= nfull << 5;
-                if (rem == 0) return false;
             }
+            for (; i < full; i++) {
+                if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                r -= step;
+                a += 32;
+            }
+            if (nh & 31)
+                if (cons.chunk(q, lane, (uint32_t)lane < (nh & 31), (int32_t)r, (int32_t)a, lp))
+                    return true;
+            rem -= nh;
+            if (rem == 0) return false;
+            b = 0;
         }
-        // general chunk: may span the end of the current run and the next run
-        const int32_t k = lenc - b;  // >= 1 leaves left in the current run
-        const bool inc = lane < k;
-        int32_t a, r;
-        if (inc) {
-            a = b + lane;
-            r = Rc - a * hin;
-        } else {
-            a = lane - k;
-            r = (a < lenn) ? Rn - a * hin : -1;
+        // the last sibling becomes the current run; step to its lex successor
+        if (np == 0) {
+            cons.fault();  // the slice claims leaves past the last one
+            return false;
         }
-        int32_t avail = k >= 32 ? 32 : min(32, k + min(lenn, 32));
-        int32_t nproc = (rem < (uint64_t)avail) ? (int32_t)rem : avail;
-        if (nproc <= 0) {
+        if (lane == np - 1) {
+            rp.a = ac + (int32_t)nsib - 1;
+            rp.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
+            rp.l = lpc + (int32_t)nsib - 1;
+        }
+        if (!warp_next_run(q, lane, hk, rp)) {
             // the slice claims leaves past the last one: only a planner fault
             // can cause this; flag it and end the walk rather than spin
             cons.fault();
             return false;
         }
-        const bool valid = lane < nproc;
-        if (cons.chunk(q, lane, valid, r, a, inc ? lpc : lpn, inc ? cs : (cs ^ 1))) return true;
-        rem -= (uint64_t)nproc;
-        if (rem == 0) return false;
-        if (nproc < k) {
-            b += nproc;
-            continue;
-        }
-        // the current run is finished: the next run becomes current
-        const int32_t used = nproc - k;
-        Rc = Rn;
-        lpc = lpn;
-        lenc = lenn;
-        cs ^= 1;
-        b = used;
-        Rn = -1;
-        lenn = 0;
-        if (warp_next_run(q, lane, hk, rp)) {
-            Rn = __shfl_sync(FULL, rp.r, np - 1);
-            lpn = __shfl_sync(FULL, rp.l, np - 1);
-            lenn = (int32_t)div32((uint32_t)Rn, q.dv_in) + 1;
-            cons.run_loaded(q, cs ^ 1, rp, lane);
-        }
-        if (b == lenc) {
-            // that run was consumed entirely by this chunk
-            Rc = Rn;
-            lpc = lpn;
-            lenc = lenn;
-            cs ^= 1;
-            b = 0;
-            Rn = -1;
-            lenn = 0;
-            if (warp_next_run(q, lane, hk, rp)) {
-                Rn = __shfl_sync(FULL, rp.r, np - 1);
-                lpn = __shfl_sync(FULL, rp.l, np - 1);
-                lenn = (int32_t)div32((uint32_t)Rn, q.dv_in) + 1;
-                cons.run_loaded(q, cs ^ 1, rp, lane);
-            }
-        }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Per-block copies of the dynamically indexed per-level constants, the slice
+// queue loop, and the device error flag.
+// ---------------------------------------------------------------------------
+struct SmemQ {
+    int32_t h[FS_MAX_D];
+    int32_t col[FS_MAX_D];
+    Div32 dvh[FS_MAX_D];
+};
+
+FS_D void load_smemq(const QueryConst& q, SmemQ& sq)
+{
+    const int t = threadIdx.x;
+    if (t < FS_MAX_D) {
+        sq.h[t] = q.h[t];
+        sq.col[t] = q.col[t];
+        sq.dvh[t] = q.dv_h[t];
+    }
+}
+
+// Walk slices with `cons`.  The planner (k_plan) has written the number of
+// slices, the number of leaves and each slice's start state.  Warp w of the
+// grid takes slice w first (no atomic: every warp starting at once on one
+// counter would serialise at L2), then pops slices W, W+1, ... (W = warps in
+// the grid) from the queue counter, one slice ahead so the atomic's latency
+// overlaps the walk.
+template <class Cons>
+FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int queue, Cons& cons)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
+    const uint64_t S = sc.ctr[CTR_SEFF];
+    const SliceSplit split(sc.ctr[CTR_L], S);
+    const uint64_t W = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
+    unsigned long long s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    while (s < S) {
+        unsigned long long nxt = 0;
+        if (lane == 0) nxt = atomicAdd(qc, 1ull) + W;
+        const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
+        cons.slice_begin(q, s);
+        bool stop = false;
+        if (k1 > k0) stop = walk_slice(q, sq.h, sq.dvh, sc.starts, s, k1 - k0, lane, hk, cons);
+        cons.slice_end(q, s);
+        if (stop) break;
+        s = __shfl_sync(FULL, nxt, 0);
+    }
+}
+
+// Sets the device error flag the host checks after a synchronous call.
+FS_D void flag_fault(uint64_t* ctr)
+{
+    if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[CTR_ERR], 1ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,8 +454,8 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh, c
 //   y0 = q u + YD[w].
 // General path: the same quantities by division.
 // ---------------------------------------------------------------------------
-template <bool TAB>
-FS_D uint32_t pair_count(const QueryConst& q, const int8_t* E, int32_t r)
+template <bool TAB, class QC>
+FS_D uint32_t pair_count(const QC& q, const int8_t* E, int32_t r)
 {
     if (TAB) {
         uint32_t qq = div32((uint32_t)r, q.dv_lcm);
@@ -329,9 +472,9 @@ FS_D uint32_t pair_count(const QueryConst& q, const int8_t* E, int32_t r)
     }
 }
 
-template <bool TAB>
-FS_D uint32_t pair_xy(const QueryConst& q, const int32_t* X0, const int32_t* YD, int32_t r,
-                      int32_t& x0, int32_t& y0)
+template <bool TAB, class QC>
+FS_D uint32_t pair_xy(const QC& q, const int32_t* X0, const int32_t* YD, int32_t r, int32_t& x0,
+                      int32_t& y0)
 {
     if (TAB) {
         uint32_t qq = div32((uint32_t)r, q.dv_lcm);
@@ -353,6 +496,56 @@ FS_D uint32_t pair_xy(const QueryConst& q, const int32_t* X0, const int32_t* YD,
         y0 = (int32_t)div32((uint32_t)(r - (int32_t)xx * q.A), q.dv_B);
         return div32(xmax - xx, q.dv_v) + 1u;
     }
+}
+
+// The pair tables for w = start, start + stride, ... < lcm (see pair_count):
+// E[w] = -1 if G does not divide w, else [w >= x0(w) A]; X0[w] = x0(w) or -1;
+// YD[w] = (w - x0(w) A) / B.  Null table pointers are skipped.
+FS_D void pair_tables_fill(const QueryConst& q, int8_t* E, int32_t* X0, int32_t* YD,
+                           uint32_t start, uint32_t stride)
+{
+    for (uint32_t w = start; w < q.lcm; w += stride) {
+        int8_t e = -1;
+        int32_t x0 = -1, yd = 0;
+        if (w % (uint32_t)q.G == 0) {
+            const uint64_t wg = w / (uint32_t)q.G;
+            const uint64_t x = ((wg % (uint64_t)q.v) * (uint64_t)q.inv) % (uint64_t)q.v;
+            const int64_t rest = (int64_t)w - (int64_t)x * q.A;  // divisible by B
+            x0 = (int32_t)x;
+            yd = (int32_t)(rest / q.B);
+            e = rest >= 0 ? 1 : 0;
+        }
+        if (E) E[w] = e;
+        if (X0) X0[w] = x0;
+        if (YD) YD[w] = yd;
+    }
+}
+
+// The pair constants alone, for consumers that keep them in registers while
+// the rest of the query's constants live in shared or global memory.
+struct PairC {
+    Div32 dv_lcm, dv_A, dv_B, dv_G, dv_v;
+    uint32_t lcm;
+    int32_t A, B, G, u, v, inv, delta;
+};
+
+FS_D PairC pair_consts(const QueryConst& q)
+{
+    PairC p;
+    p.dv_lcm = q.dv_lcm;
+    p.dv_A = q.dv_A;
+    p.dv_B = q.dv_B;
+    p.dv_G = q.dv_G;
+    p.dv_v = q.dv_v;
+    p.lcm = q.lcm;
+    p.A = q.A;
+    p.B = q.B;
+    p.G = q.G;
+    p.u = q.u;
+    p.v = q.v;
+    p.inv = q.inv;
+    p.delta = q.delta;
+    return p;
 }
 
 // warp sums

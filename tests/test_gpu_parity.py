@@ -31,6 +31,9 @@ PAIR = fs.make_config(method=fs.METHOD_PAIR)
 PLAIN_KEEP = fs.make_config(method=fs.METHOD_PLAIN, keep_order=True)
 PAIR_KEEP = fs.make_config(method=fs.METHOD_PAIR, keep_order=True)
 CONFIGS = {"pair": PAIR, "plain": PLAIN, "pair_keep": PAIR_KEEP, "plain_keep": PLAIN_KEEP}
+TRIPLE = fs.make_config(method=fs.METHOD_TRIPLE)
+TRIPLE_KEEP = fs.make_config(method=fs.METHOD_TRIPLE, keep_order=True)
+AUTO = fs.make_config()
 
 
 def lexsort_rows(a):
@@ -72,6 +75,33 @@ def test_count_random(method):
     cfg = CONFIGS[method]
     for n, g in medium_cases():
         assert fs.fs_count(n, g, cfg) == oracle.count_dp(n, g), (n, g)
+
+
+@pytest.mark.parametrize("cfg", [TRIPLE, TRIPLE_KEEP, AUTO], ids=["triple", "triple_keep", "auto"])
+def test_count_triple(cfg):
+    """The trailing-three tables (Sec. 6.1) give the same counts; explicit
+    TRIPLE refuses d < 4, AUTO falls back to PAIR there."""
+    for n, g in medium_cases():
+        if len(g) < 4 and cfg is not AUTO:
+            with pytest.raises(fs.FsError) as e:
+                fs.fs_count(n, g, cfg)
+            assert e.value.status == fs.FS_E_NOTIMPL
+            continue
+        assert fs.fs_count(n, g, cfg) == oracle.count_dp(n, g), (n, g)
+
+
+def test_length_min_max_triple():
+    """fs_length_stats without a histogram (TRIPLE under AUTO): count, min, max."""
+    for n, g in medium_cases():
+        mm = oracle.minmax_dp(n, g) or (0, 0)
+        expect = (oracle.count_dp(n, g),) + tuple(mm)
+        assert fs.fs_length_stats(n, g, None, AUTO) == expect, (n, g)
+        if len(g) >= 4:
+            assert fs.fs_length_stats(n, g, None, TRIPLE) == expect, (n, g)
+    with pytest.raises(fs.FsError) as e:  # a histogram needs the PAIR walk
+        h = torch.zeros(1000, dtype=torch.int64, device="cuda")
+        fs.fs_length_stats(300, (11, 13, 17, 19), h, TRIPLE)
+    assert e.value.status == fs.FS_E_NOTIMPL
 
 
 def test_count_table1_pins_and_errata():
@@ -291,7 +321,7 @@ def test_plan_and_slice_counts_match_oracle(slices):
     disjoint, cover Z, and are balanced in leaves."""
     for n, g in [(600, (13, 37, 38, 40)), (200, (11, 13, 17, 19, 23)), (300, (7, 5, 3)),
                  workloads.CONFIG1]:
-        order, bounds, leaves = fs.fs_plan(n, g, slices)
+        order, bounds, leaves = fs.fs_plan(n, g, slices, PAIR)
         wg = walk_gens(g, order)
         for method in (fs.METHOD_PAIR, fs.METHOD_PLAIN):
             counts = fs.fs_slice_counts(n, g, slices, fs.make_config(method=method))
@@ -318,12 +348,34 @@ def test_plan_and_slice_counts_match_oracle(slices):
             assert len(live) == slices
 
 
+@pytest.mark.parametrize("slices", [1, 3, 64, 2000])
+def test_triple_slices_match_oracle(slices):
+    """TRIPLE slices cut the prefixes one level shorter; each slice still holds
+    exactly what the oracle's bounded stream finds between its bounds."""
+    for n, g in [(600, (13, 37, 38, 40)), (250, (11, 13, 17, 19, 23)), workloads.CONFIG1]:
+        order, bounds, leaves = fs.fs_plan(n, g, slices, TRIPLE)
+        counts = fs.fs_slice_counts(n, g, slices, TRIPLE)
+        wg = walk_gens(g, order)
+        total = 0
+        for s_ in range(slices):
+            lo = bounds[s_]
+            if lo[0] < 0:
+                assert counts[s_] == 0
+                continue
+            assert lo[-1] == 0 and lo[-2] == 0 and lo[-3] == 0
+            hi = bounds[s_ + 1] if bounds[s_ + 1][0] >= 0 else None
+            c, _, _, _, _ = oracle.range_stats(n, wg, lo, hi, with_hist=False)
+            assert counts[s_] == c, (n, g, s_)
+            total += c
+        assert total == oracle.count_dp(n, g)
+
+
 def test_enumerate_slices_sampled_against_oracle_stream():
     """Rows of sampled slices equal the oracle's bounded stream for the same
     bounds (reversed to ascending), at their scanned offsets."""
     n, g = 1200, (13, 37, 38, 40, 41)
     S = 257
-    cfg = fs.make_config(slices=S)
+    cfg = fs.make_config(method=fs.METHOD_PAIR, slices=S)
     order, bounds, _ = fs.fs_plan(n, g, S, cfg)
     counts = fs.fs_slice_counts(n, g, S, cfg)
     offs = np.concatenate([[0], np.cumsum(counts)])
@@ -361,7 +413,7 @@ def test_config2_full():
     assert np.array_equal(hist.cpu().numpy().astype(np.uint64), oracle.length_dp(n, g))
     d = len(g)
     S = 4096
-    cfg = fs.make_config(slices=S)
+    cfg = fs.make_config(method=fs.METHOD_PAIR, slices=S)
     out = torch.empty(expect * d, dtype=torch.int32, device="cuda")
     assert fs.fs_enumerate(n, g, out, cfg=cfg) == expect
     rows = out.view(-1, d)
@@ -403,9 +455,11 @@ def test_config3_count_and_lengths_dp_exact():
     assert cnt == expect
     assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref)
     assert (mn, mx) == oracle.minmax_dp(n, g)
+    assert fs.fs_count(n, g, PAIR) == expect
+    assert fs.fs_length_stats(n, g, None) == (expect,) + oracle.minmax_dp(n, g)
     S = 1 << 20
-    order, bounds, leaves = fs.fs_plan(n, g, S)
-    counts = fs.fs_slice_counts(n, g, S)
+    order, bounds, leaves = fs.fs_plan(n, g, S, PAIR)
+    counts = fs.fs_slice_counts(n, g, S, PAIR)
     assert sum(counts) == expect
     wg = walk_gens(g, order)
     rng = np.random.default_rng(9)
@@ -419,3 +473,4 @@ def test_config3_count_and_lengths_dp_exact():
 def test_config3_other_seeds(seed):
     n, g = workloads.config3(seed)
     assert fs.fs_count(n, g) == oracle.count_dp(n, g)
+    assert fs.fs_count(n, g, PAIR) == oracle.count_dp(n, g)
