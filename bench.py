@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -318,6 +320,8 @@ def run_gpu(args):
     extras = None
     if not args.no_extras:
         extras = heavy_count_extras(fs, workloads, dev)
+        extras["batched"] = batch_extras(fs, workloads, dev)
+        extras["serving"] = serving_extras(fs, workloads, args.serve_rate, args.serve_requests)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----
     cpu = None
@@ -410,6 +414,117 @@ def heavy_count_extras(fs, workloads, dev):
     }
 
 
+def batch_extras(fs, workloads, dev):
+    """The batched workload (4096 seeded queries, d in [3, 8], generators in
+    [5, 100], n in [100, 5000]): one persistent launch per batch, autotuned,
+    against one single-query call per query, at equal exact counts."""
+    import torch
+    qs = workloads.config4(0)
+    out = {"workload": "4096 batched queries, d in [3,8], distinct gens in [5,100], n in [100,5000] (seed 0)"}
+    reps = 5
+    counts = None
+    for mode, name in ((fs.BATCH_COUNT, "count"), (fs.BATCH_LENGTHS, "lengths")):
+        best, tune_ms = fs.fs_batch_autotune(qs, mode)
+        with fs.Batch(qs, mode, best) as b:
+            b.launch()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                b.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res = b.results()
+        if counts is None:
+            counts = [r[0] for r in res]
+        assert [r[0] for r in res] == counts
+        out[f"persistent_{name}_ms"] = ms
+        out[f"persistent_{name}_queries_per_s"] = len(qs) / (ms / 1000.0)
+        out[f"autotuned_{name}"] = {"block_threads": best.block_threads,
+                                    "blocks_per_sm": best.blocks_per_sm, "items": best.slices}
+    out["factorizations"] = sum(counts)
+    dcs = torch.zeros(len(qs), dtype=torch.int64, device=dev)
+    for i, (n, g) in enumerate(qs):  # warm-up of the per-query path
+        fs.fs_count_async(n, g, dcs[i:i + 1])
+    torch.cuda.synchronize()
+    dcs.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i, (n, g) in enumerate(qs):
+        fs.fs_count_async(n, g, dcs[i:i + 1])
+    e1.record()
+    torch.cuda.synchronize()
+    per_ms = e0.elapsed_time(e1)
+    assert [int(x) for x in dcs.tolist()] == counts  # equal exact results
+    out["per_query_count_ms"] = per_ms
+    out["per_query_queries_per_s"] = len(qs) / (per_ms / 1000.0)
+    out["persistent_speedup_count"] = per_ms / out["persistent_count_ms"]
+    return out
+
+
+def serving_extras(fs, workloads, rate: float, nreq: int):
+    """The serving workload: Poisson arrivals of queries drawn like the batched
+    ones with n up to 20000, 80 % count / 15 % length statistics / 5 %
+    enumerate (int16 rows), through the continuous-batching request loop; a
+    client thread releases enumerate rows as soon as they are polled."""
+    import threading
+    reqs = workloads.config5(0, nreq, rate, 20000)
+    budget = 32 << 30
+    srv = fs.Server(mem_budget_bytes=budget, table_bytes=1 << 30, max_batch=512, slots=3,
+                    window_us=200)
+    try:
+        warm = [srv.submit(op, n, g) for (_, op, n, g) in reqs[:16]]
+        seen = 0
+        while seen < len(warm):
+            for r in srv.poll(64, wait_ms=50):
+                seen += 1
+                if r["op"] == fs.REQ_ENUMERATE and r["status"] == fs.FS_OK:
+                    srv.release(r["ticket"])
+        done = {}
+
+        def poller():
+            while len(done) < nreq:
+                for r in srv.poll(1024, wait_ms=20):
+                    done[r["ticket"]] = r
+                    if r["op"] == fs.REQ_ENUMERATE and r["status"] == fs.FS_OK:
+                        srv.release(r["ticket"])
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for (ta, op, n, g) in reqs:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            srv.submit(op, n, g, elem_bytes=2)
+        th.join()
+    finally:
+        srv.close()
+    rs = list(done.values())
+    lat = np.array([r["t_done"] - r["t_submit"] for r in rs]) * 1000.0
+    span = max(r["t_done"] for r in rs) - min(r["t_submit"] for r in rs)
+    by_op = {}
+    for op, name in ((fs.REQ_COUNT, "count"), (fs.REQ_LENGTHS, "lengths"),
+                     (fs.REQ_ENUMERATE, "enumerate")):
+        l = np.array([(r["t_done"] - r["t_submit"]) * 1000.0 for r in rs if r["op"] == op])
+        if l.size:
+            by_op[name] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)),
+                           "p99_ms": float(np.percentile(l, 99))}
+    status = {}
+    for r in rs:
+        status[fs.status_name(r["status"])] = status.get(fs.status_name(r["status"]), 0) + 1
+    return {
+        "workload": (f"{nreq} requests, Poisson arrivals at {rate:g}/s, d in [3,8], gens in "
+                     f"[5,100], n in [100,20000], 80/15/5 % count/lengths/enumerate (int16), seed 0"),
+        "server": {"mem_budget_bytes": budget, "max_batch": 512, "slots": 3, "window_us": 200},
+        "queries_per_s": nreq / span, "span_s": span,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "by_op": by_op, "status": status,
+        "factorizations_served": int(sum(r["count"] for r in rs if r["status"] == fs.FS_OK)),
+    }
+
+
 def run_profile_case(args):
     """Small cases of the same kernels for ncu captures, a few calls each:
     "enum": the single-large-query generators at a smaller n (output still
@@ -457,6 +572,9 @@ def main():
     ap.add_argument("--profile-case", choices=["enum", "count", "count_triple"], default=None,
                     help="run only a small case of the same kernels (for ncu)")
     ap.add_argument("--profile-n", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=1000.0,
+                    help="serving extras: Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

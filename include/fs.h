@@ -235,9 +235,30 @@ typedef struct fs_batch fs_batch;  /* opaque; owns its device memory */
  * batch's device memory on the current device and uploads the per-query
  * constants.  Invalid queries are kept with a non-OK status and skipped.
  * mode: FS_BATCH_COUNT or FS_BATCH_LENGTHS.  cfg (nullable): block_threads
- * (<= 256), blocks_per_sm, slices (= work items of the whole batch). */
+ * (<= 256), blocks_per_sm, slices (= work items of the whole batch), method
+ * (FS_METHOD_PAIR: every query walks its first d-2 levels; otherwise queries
+ * with d >= 4 use the trailing-three tables of FS_METHOD_TRIPLE). */
 fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_config* cfg,
                           fs_batch** out);
+/* Reusable batches for request loops: reserve once, then load / launch /
+ * fetch / collect any number of times without allocating or synchronising.
+ * fs_batch_table_bytes: host-only, the table bytes `queries` need.
+ * fs_batch_reserve: room for max_queries queries and table_bytes of tables
+ *   (allocates all device and pinned host memory of the batch).
+ * fs_batch_load: plans the queries on the host and uploads their constants
+ *   on `stream` from the batch's pinned buffer; FS_E_CAPACITY if they exceed
+ *   the reservation.  Do not load again before that copy has run (order it on
+ *   the same stream, or wait).
+ * fs_batch_fetch: enqueues the copy of the results into pinned host memory.
+ * fs_batch_collect: reads the fetched results; the caller waits for the
+ *   stream (or an event recorded after fs_batch_fetch) first. */
+fs_status fs_batch_table_bytes(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                               uint64_t* bytes);
+fs_status fs_batch_reserve(int max_queries, uint64_t table_bytes, int mode, const fs_config* cfg,
+                           fs_batch** out);
+fs_status fs_batch_load(fs_batch* b, const fs_query* queries, int nq, void* stream);
+fs_status fs_batch_fetch(fs_batch* b, void* stream);
+fs_status fs_batch_collect(fs_batch* b, fs_result* results);
 /* Enqueues one complete evaluation of the batch on `stream` (tables, plan,
  * walk); nothing is allocated and nothing synchronises, so it can be
  * repeated or captured into a CUDA graph. */
@@ -255,6 +276,86 @@ fs_status fs_batch_run(const fs_query* queries, int nq, int mode, const fs_confi
  * nullable).  Every candidate computes the same exact results. */
 fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config* best,
                             double* best_ms, void* stream);
+
+/* Grows the library's per-device scratch to at least `bytes` now (it is
+ * otherwise grown on demand, which synchronises the device).  Call before
+ * stream capture or before a latency-sensitive loop. */
+fs_status fs_reserve(uint64_t bytes);
+
+/* --- serving: a request loop with continuous batching -------------------- */
+
+/* The paper evaluates one query at a time; this loop serves a stream of them.
+ * fs_server_submit queues a request and returns at once.  A worker thread
+ * admits the queued requests into `slots` reusable batches (fs_batch_reserve),
+ * each on its own stream: a free slot takes up to max_batch queued requests
+ * (when other batches are running it first lets the batch fill for up to
+ * window_us), so requests that arrive while earlier ones are on the GPU are
+ * batched and run concurrently with them.  An ENUMERATE request is counted in
+ * a batch first; its rows (count * d * elem_bytes bytes, exact) are then
+ * admitted against the device memory budget: larger than the whole budget ->
+ * FS_E_CAPACITY (count still reported); otherwise it waits until that many
+ * bytes are free, is materialised (fs_enumerate_async, one at a time, on the
+ * server's enumerate stream) and its rows stay reserved until
+ * fs_server_release.  Results are exactly those of the single-query calls.
+ * A single query whose tables exceed table_bytes is answered FS_E_CAPACITY.
+ * Thread safety: submit / poll / release may be called from any thread.
+ * The server uses the library's shared per-device scratch for its enumerates:
+ * do not run other asynchronous library calls on the same device while it
+ * lives, unless ordered after fs_server_destroy. */
+enum { FS_REQ_COUNT = 0, FS_REQ_LENGTHS = 1, FS_REQ_ENUMERATE = 2 };
+
+typedef struct fs_server_config {
+    uint64_t mem_budget_bytes;  /* device bytes for enumerate rows; 0 = 1 GiB */
+    uint64_t table_bytes;       /* table bytes per batch slot; 0 = 256 MiB */
+    int32_t max_batch;          /* queries per batch; 0 = 512 */
+    int32_t slots;              /* batches in flight; 0 = 3 */
+    int32_t window_us;          /* fill window while the GPU is busy; 0 = 200 */
+    int32_t pad;
+} fs_server_config;
+
+typedef struct fs_request {
+    int64_t n;
+    int32_t d;
+    uint32_t gens[FS_MAX_D];  /* as fs_count */
+    int32_t op;               /* FS_REQ_* */
+    int32_t elem_bytes;       /* ENUMERATE: 2 (int16) or 4 (int32) */
+    int32_t keep_order;       /* ENUMERATE: row order as fs_config.keep_order */
+    int32_t pad;
+} fs_request;
+
+typedef struct fs_response {
+    uint64_t ticket;
+    int32_t status;     /* FS_OK or the fs_status that rejected the request */
+    int32_t op;
+    uint64_t count;     /* |Z(n, g)| (also for a rejected ENUMERATE when it was counted) */
+    uint32_t min_len;   /* LENGTHS and ENUMERATE: min / max of sum a_i when count > 0 */
+    uint32_t max_len;
+    void* rows;         /* ENUMERATE, FS_OK: DEVICE rows [count][d], as fs_enumerate_ex
+                           with the request's keep_order; owned by the server until
+                           fs_server_release(ticket) */
+    double t_submit;    /* seconds since fs_server_create */
+    double t_start;     /* when its batch (or its enumerate) was launched */
+    double t_done;      /* when its result was seen complete */
+} fs_response;
+
+typedef struct fs_server fs_server;  /* opaque */
+
+/* Creates the server on the current device (cfg nullable = defaults) and
+ * allocates everything it uses: the batch slots, their streams, the row
+ * budget.  FS_E_NOMEM / FS_E_CUDA if that fails. */
+fs_status fs_server_create(const fs_server_config* cfg, fs_server** out);
+/* Queues *req (copied); *ticket (host) identifies its response.  FS_E_INVAL for
+ * a bad op or elem_bytes; invalid queries are answered with their status. */
+fs_status fs_server_submit(fs_server* s, const fs_request* req, uint64_t* ticket);
+/* Moves up to `max` completed responses into out (host), oldest first;
+ * *got = how many.  Waits up to wait_ms milliseconds when none is ready. */
+fs_status fs_server_poll(fs_server* s, fs_response* out, int max, int* got, int wait_ms);
+/* Returns the rows of an ENUMERATE response to the budget.  FS_E_INVAL if the
+ * ticket holds no rows. */
+fs_status fs_server_release(fs_server* s, uint64_t ticket);
+/* Finishes every queued request, then frees the server; rows not yet released
+ * are freed with it. */
+fs_status fs_server_destroy(fs_server* s);
 
 /* --- kernel timing ------------------------------------------------------ */
 

@@ -57,6 +57,27 @@ class fs_result(ctypes.Structure):
 
 
 BATCH_COUNT, BATCH_LENGTHS = 0, 1
+REQ_COUNT, REQ_LENGTHS, REQ_ENUMERATE = 0, 1, 2
+
+
+class fs_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
+                ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("window_us", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class fs_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("gens", ctypes.c_uint32 * MAX_D),
+                ("op", ctypes.c_int32), ("elem_bytes", ctypes.c_int32),
+                ("keep_order", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class fs_response(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("count", ctypes.c_uint64), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32), ("rows", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -101,6 +122,21 @@ SIGNATURES = {
                                     ctypes.POINTER(fs_result), _vp]),
     "fs_batch_autotune": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int,
                                          _cfgp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "fs_batch_table_bytes": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int,
+                                            _cfgp, _u64p]),
+    "fs_batch_reserve": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _cfgp,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "fs_batch_load": (ctypes.c_int, [_vp, ctypes.POINTER(fs_query), ctypes.c_int, _vp]),
+    "fs_batch_fetch": (ctypes.c_int, [_vp, _vp]),
+    "fs_batch_collect": (ctypes.c_int, [_vp, ctypes.POINTER(fs_result)]),
+    "fs_reserve": (ctypes.c_int, [ctypes.c_uint64]),
+    "fs_server_create": (ctypes.c_int, [ctypes.POINTER(fs_server_config),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "fs_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(fs_request), _u64p]),
+    "fs_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(fs_response), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "fs_server_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "fs_server_destroy": (ctypes.c_int, [_vp]),
     "fs_profile_enable": (None, [ctypes.c_int]),
     "fs_profile_read": (ctypes.c_int, [ctypes.c_char_p, _u64p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int]),
@@ -327,6 +363,70 @@ class Batch:
     def close(self):
         if self._h:
             lib().fs_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fs_reserve(nbytes: int) -> None:
+    """Grow the library's per-device scratch to at least nbytes now."""
+    _check(lib().fs_reserve(int(nbytes)))
+
+
+class Server:
+    """The request loop of fs_server_*: submit() queues a request and returns
+    its ticket, poll() returns completed responses as dicts.  An ENUMERATE
+    response's rows stay on the device (``rows`` = device address, [count][d]
+    of int16 / int32) until release(ticket)."""
+
+    def __init__(self, mem_budget_bytes: int = 0, table_bytes: int = 0, max_batch: int = 0,
+                 slots: int = 0, window_us: int = 0):
+        cfg = fs_server_config(int(mem_budget_bytes), int(table_bytes), int(max_batch),
+                               int(slots), int(window_us), 0)
+        h = ctypes.c_void_p(0)
+        _check(lib().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, op: int, n: int, gens, elem_bytes: int = 2, keep_order: bool = False) -> int:
+        g = [int(x) for x in gens]
+        r = fs_request()
+        r.n = int(n)
+        r.d = len(g)
+        for j, x in enumerate(g[:MAX_D]):
+            r.gens[j] = x & 0xffffffff
+        r.op = int(op)
+        r.elem_bytes = int(elem_bytes)
+        r.keep_order = 1 if keep_order else 0
+        t = ctypes.c_uint64(0)
+        _check(lib().fs_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, max_items: int = 256, wait_ms: int = 0):
+        out = (fs_response * max_items)()
+        got = ctypes.c_int(0)
+        _check(lib().fs_server_poll(self._h, out, int(max_items), ctypes.byref(got), int(wait_ms)))
+        return [dict(ticket=int(r.ticket), status=int(r.status), op=int(r.op),
+                     count=int(r.count), min_len=int(r.min_len), max_len=int(r.max_len),
+                     rows=int(r.rows or 0), t_submit=float(r.t_submit),
+                     t_start=float(r.t_start), t_done=float(r.t_done))
+                for r in out[:got.value]]
+
+    def release(self, ticket: int) -> None:
+        _check(lib().fs_server_release(self._h, int(ticket)))
+
+    def close(self):
+        if self._h:
+            lib().fs_server_destroy(self._h)
             self._h = None
 
     def __enter__(self):

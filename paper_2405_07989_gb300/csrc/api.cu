@@ -280,13 +280,7 @@ int method_of(const fs_config& c)
 QueryConst reduce_triple(const QueryConst& q)
 {
     QueryConst r = q;
-    r.D = q.D - 1;
-    r.P = q.P - 1;
-    r.dv_in = q.dv_h[r.P - 1];
-    r.nw = r.P - 1;
-    r.tab_e = 0;
-    r.tab_xy = 0;
-    r.lcm = 0;
+    reduce_to_triple(r);
     return r;
 }
 
@@ -792,6 +786,15 @@ fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_confi
     return FS_OK;
 }
 
+fs_status fs_reserve(uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState* ds = nullptr;
+    fs_status s = get_dev(&ds);
+    if (s != FS_OK) return s;
+    return ensure_arena(ds, (size_t)bytes);
+}
+
 void fs_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -850,10 +853,16 @@ fs_status fs_probe_int_rate(int kind, uint32_t iters, double* ops_per_s)
 
 struct fs_batch {
     int dev = -1;
-    int nq = 0;
+    int nq = 0;          // queries loaded
+    int cap_q = 0;       // queries reserved
+    uint64_t cap_arena = 0;
     int mode = 0;
+    fs_config cfg;
     std::vector<int32_t> status;
     void* mem = nullptr;
+    BatchQ* hq = nullptr;       // pinned: constants to upload
+    BatchRes* hres = nullptr;   // pinned: fetched results
+    uint64_t* hctr = nullptr;   // pinned: fetched counters
     BatchDev bd;
     int threads = 256;
     int blocks = 0;
@@ -875,58 +884,92 @@ fs_status batch_shape(fs_batch* b, int threads, int blocks_per_sm, uint64_t item
     b->blocks = b->sms * bps;
     const uint64_t warps = (uint64_t)b->blocks * (threads / 32);
     uint64_t target = items > 0 ? items : warps * 8;
-    if (target + (uint64_t)b->nq > b->bd.items_cap) target = b->bd.items_cap - (uint64_t)b->nq;
+    if (target + (uint64_t)b->cap_q > b->bd.items_cap) target = b->bd.items_cap - (uint64_t)b->cap_q;
     if (target < 1) target = 1;
     b->bd.items_target = target;
     return FS_OK;
+}
+
+// Host-side planning of queries into BatchQ records (in `out`), their table
+// offsets and statuses; returns the table bytes they need.
+uint64_t batch_plan_host(const fs_query* queries, int nq, int mode, const fs_config& cc, BatchQ* out,
+                         int32_t* status)
+{
+    uint64_t arena = 0;
+    auto take = [&](size_t bytes) {
+        const uint64_t o = arena;
+        arena += (bytes + 15) & ~(size_t)15;
+        return o;
+    };
+    fs_config walk_cfg = cfg_or_default(nullptr);  // descending walk order
+    for (int i = 0; i < nq; i++) {
+        BatchQ& B = out[i];
+        memset(&B, 0, sizeof B);
+        const fs_query& Q = queries[i];
+        Query qq;
+        fs_status s = FS_E_INVAL;
+        if (Q.d >= 1 && Q.d <= FS_MAX_D) s = build_query(Q.n, Q.gens, Q.d, walk_cfg, qq);
+        status[i] = s;
+        if (s != FS_OK) continue;
+        B.q = qq.q;
+        B.valid = 1;
+        // the trailing-three tables unless PAIR is asked for
+        B.triple = cc.method != FS_METHOD_PAIR && B.q.D >= 4 && B.q.n < (1 << 27);
+        const size_t n1 = (size_t)B.q.n + 1;
+        if (B.triple) {
+            B.off_W = take((size_t)(B.q.nw - 1) * n1 * 8);
+            B.off_T3 = take(n1 * 8);
+            B.off_MN3 = take(mode == FS_BATCH_LENGTHS ? n1 * 4 : 0);
+            B.off_MX3 = take(mode == FS_BATCH_LENGTHS ? n1 * 4 : 0);
+        } else {
+            B.off_W = take((size_t)B.q.nw * n1 * 8);
+            B.off_E = take(B.q.tab_e ? B.q.lcm : 0);
+            const bool xy = mode == FS_BATCH_LENGTHS && B.q.tab_xy;
+            B.off_X0 = take(xy ? (size_t)B.q.lcm * 4 : 0);
+            B.off_YD = take(xy ? (size_t)B.q.lcm * 4 : 0);
+        }
+    }
+    return arena;
+}
+
+void batch_free(fs_batch* b)
+{
+    if (b->mem) cudaFree(b->mem);
+    if (b->hq) cudaFreeHost(b->hq);
+    if (b->hres) cudaFreeHost(b->hres);
+    delete b;
 }
 
 }  // namespace
 
 extern "C" {
 
-fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_config* cfg,
-                          fs_batch** out)
+fs_status fs_batch_table_bytes(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                               uint64_t* bytes)
 {
-    if (!queries || !out || nq < 1) return fail(FS_E_INVAL, "batch: queries / out NULL or nq < 1");
+    if (!queries || !bytes || nq < 1) return fail(FS_E_INVAL, "batch: queries / bytes NULL or nq < 1");
+    std::vector<BatchQ> tmp(nq);
+    std::vector<int32_t> st(nq);
+    *bytes = batch_plan_host(queries, nq, mode, cfg_or_default(cfg), tmp.data(), st.data());
+    return FS_OK;
+}
+
+fs_status fs_batch_reserve(int max_queries, uint64_t table_bytes, int mode, const fs_config* cfg,
+                           fs_batch** out)
+{
+    if (!out || max_queries < 1) return fail(FS_E_INVAL, "batch: out NULL or max_queries < 1");
     if (mode != FS_BATCH_COUNT && mode != FS_BATCH_LENGTHS) return fail(FS_E_INVAL, "batch mode %d", mode);
     std::lock_guard<std::mutex> lk(g_mu);
     fs_config cc = cfg_or_default(cfg);
-    fs_config walk_cfg = cfg_or_default(nullptr);  // descending walk order
     fs_batch* b = new fs_batch;
-    b->nq = nq;
+    b->cap_q = max_queries;
+    b->cap_arena = table_bytes;
     b->mode = mode;
-    b->status.assign(nq, FS_OK);
-    std::vector<BatchQ> hq(nq);
-    size_t arena = 0;
-    auto take = [&](size_t bytes) {
-        const size_t o = arena;
-        arena += (bytes + 15) & ~(size_t)15;
-        return (uint64_t)o;
-    };
-    for (int i = 0; i < nq; i++) {
-        BatchQ& B = hq[i];
-        memset(&B, 0, sizeof B);
-        const fs_query& Q = queries[i];
-        Query qq;
-        fs_status s = FS_E_INVAL;
-        if (Q.d >= 1 && Q.d <= FS_MAX_D) s = build_query(Q.n, Q.gens, Q.d, walk_cfg, qq);
-        if (s != FS_OK) {
-            b->status[i] = s;
-            continue;
-        }
-        B.q = qq.q;
-        B.valid = 1;
-        B.off_W = take((size_t)B.q.nw * (size_t)(B.q.n + 1) * 8);
-        B.off_E = take(B.q.tab_e ? B.q.lcm : 0);
-        const bool xy = mode == FS_BATCH_LENGTHS && B.q.tab_xy;
-        B.off_X0 = take(xy ? (size_t)B.q.lcm * 4 : 0);
-        B.off_YD = take(xy ? (size_t)B.q.lcm * 4 : 0);
-    }
+    b->cfg = cc;
     cudaError_t e = cudaGetDevice(&b->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
     if (e != cudaSuccess) {
-        delete b;
+        batch_free(b);
         return cuda_fail(e, "no CUDA device");
     }
     // items: room for the largest shape the autotuner tries (32 per warp at
@@ -935,38 +978,107 @@ fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_co
     batch_walk_occupancy(mode, 256, &bps);
     const uint64_t max_items = std::max<uint64_t>((uint64_t)std::max(cc.slices, (int64_t)0),
                                                   (uint64_t)b->sms * std::max(bps, 1) * 8 * 32);
-    b->bd.items_cap = max_items + (uint64_t)nq;
+    b->bd.items_cap = max_items + (uint64_t)max_queries;
     const size_t off_qs = 0;
-    const size_t off_res = al(off_qs + sizeof(BatchQ) * (size_t)nq);
-    const size_t off_ctr = al(off_res + sizeof(BatchRes) * (size_t)nq);
+    const size_t off_res = al(off_qs + sizeof(BatchQ) * (size_t)max_queries);
+    const size_t off_ctr = al(off_res + sizeof(BatchRes) * (size_t)max_queries);
     const size_t off_st = al(off_ctr + BCTR_N * 8);
     const size_t off_ar = al(off_st + (size_t)b->bd.items_cap * START_W * 4);
-    const size_t total = al(off_ar + arena);
+    const size_t total = al(off_ar + table_bytes);
     e = cudaMalloc(&b->mem, total);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->hq, sizeof(BatchQ) * (size_t)max_queries);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void**)&b->hres, sizeof(BatchRes) * (size_t)max_queries + BCTR_N * 8);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        delete b;
-        return fail(FS_E_NOMEM, "batch cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+        batch_free(b);
+        return fail(FS_E_NOMEM, "batch reserve (%zu device bytes): %s", total, cudaGetErrorString(e));
     }
+    b->hctr = (uint64_t*)(b->hres + max_queries);
     char* base = (char*)b->mem;
     b->bd.qs = (BatchQ*)(base + off_qs);
-    b->bd.nq = nq;
+    b->bd.nq = 0;
     b->bd.mode = mode;
     b->bd.arena = (unsigned char*)(base + off_ar);
     b->bd.starts = (int32_t*)(base + off_st);
     b->bd.ctr = (uint64_t*)(base + off_ctr);
     b->bd.res = (BatchRes*)(base + off_res);
     b->bd.min_leaves = 64;
-    e = cudaMemcpy(b->bd.qs, hq.data(), sizeof(BatchQ) * (size_t)nq, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(b->mem);
-        delete b;
-        return cuda_fail(e, "batch upload");
-    }
     fs_status s = batch_shape(b, cc.block_threads, cc.blocks_per_sm, (uint64_t)std::max(cc.slices, (int64_t)0));
     if (s != FS_OK) {
-        cudaFree(b->mem);
-        delete b;
+        batch_free(b);
+        return s;
+    }
+    *out = b;
+    return FS_OK;
+}
+
+fs_status fs_batch_load(fs_batch* b, const fs_query* queries, int nq, void* stream)
+{
+    if (!b || !queries || nq < 1) return fail(FS_E_INVAL, "batch: NULL or nq < 1");
+    if (nq > b->cap_q) return fail(FS_E_CAPACITY, "batch: %d queries, room for %d", nq, b->cap_q);
+    std::lock_guard<std::mutex> lk(g_mu);
+    b->status.assign(nq, FS_OK);
+    const uint64_t need = batch_plan_host(queries, nq, b->mode, b->cfg, b->hq, b->status.data());
+    if (need > b->cap_arena)
+        return fail(FS_E_CAPACITY, "batch: tables need %llu bytes, room for %llu",
+                    (unsigned long long)need, (unsigned long long)b->cap_arena);
+    cudaError_t e = cudaMemcpyAsync(b->bd.qs, b->hq, sizeof(BatchQ) * (size_t)nq,
+                                    cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+    b->nq = nq;
+    b->bd.nq = nq;
+    return FS_OK;
+}
+
+fs_status fs_batch_fetch(fs_batch* b, void* stream)
+{
+    if (!b || b->nq < 1) return fail(FS_E_INVAL, "batch: NULL or nothing loaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(b->hres, b->bd.res, sizeof(BatchRes) * (size_t)b->nq,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->hctr, b->bd.ctr, BCTR_N * 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fetch");
+    return FS_OK;
+}
+
+fs_status fs_batch_collect(fs_batch* b, fs_result* results)
+{
+    if (!b || !results) return fail(FS_E_INVAL, "batch / results is NULL");
+    if (b->hctr[BCTR_ERR]) return fail(FS_E_CUDA, "internal error in the batch walk (flags %llx)",
+                                       (unsigned long long)b->hctr[BCTR_ERR]);
+    for (int i = 0; i < b->nq; i++) {
+        fs_result& R = results[i];
+        R.count = b->hres[i].count;
+        R.status = b->status[i];
+        R.pad = 0;
+        if (b->mode == FS_BATCH_LENGTHS && R.count > 0) {
+            R.min_len = (uint32_t)(0xffffffffu - b->hres[i].minc);
+            R.max_len = (uint32_t)b->hres[i].max;
+        } else {
+            R.min_len = R.max_len = 0;
+        }
+    }
+    return FS_OK;
+}
+
+fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_config* cfg,
+                          fs_batch** out)
+{
+    if (!queries || !out || nq < 1) return fail(FS_E_INVAL, "batch: queries / out NULL or nq < 1");
+    uint64_t bytes = 0;
+    fs_status s = fs_batch_table_bytes(queries, nq, mode, cfg, &bytes);
+    if (s != FS_OK) return s;
+    fs_batch* b = nullptr;
+    s = fs_batch_reserve(nq, bytes, mode, cfg, &b);
+    if (s != FS_OK) return s;
+    s = fs_batch_load(b, queries, nq, nullptr);
+    if (s == FS_OK) {
+        cudaError_t e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) s = cuda_fail(e, "batch upload");
+    }
+    if (s != FS_OK) {
+        batch_free(b);
         return s;
     }
     *out = b;
@@ -975,7 +1087,7 @@ fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_co
 
 fs_status fs_batch_launch(fs_batch* b, void* stream)
 {
-    if (!b) return fail(FS_E_INVAL, "batch is NULL");
+    if (!b || b->nq < 1) return fail(FS_E_INVAL, "batch is NULL or has no queries loaded");
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = (cudaStream_t)stream;
     ProfScope ps("batch", st, 4);
@@ -989,38 +1101,19 @@ fs_status fs_batch_launch(fs_batch* b, void* stream)
 fs_status fs_batch_results(fs_batch* b, fs_result* results, void* stream)
 {
     if (!b || !results) return fail(FS_E_INVAL, "batch / results is NULL");
-    std::lock_guard<std::mutex> lk(g_mu);
-    cudaStream_t st = (cudaStream_t)stream;
-    std::vector<BatchRes> hr(b->nq);
-    uint64_t hc[BCTR_N];
-    cudaError_t e = cudaMemcpyAsync(hr.data(), b->bd.res, sizeof(BatchRes) * (size_t)b->nq,
-                                    cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, b->bd.ctr, sizeof hc, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    fs_status s = fs_batch_fetch(b, stream);
+    if (s != FS_OK) return s;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch execution");
-    if (hc[BCTR_ERR]) return fail(FS_E_CUDA, "internal error in the batch walk (flags %llx)",
-                                  (unsigned long long)hc[BCTR_ERR]);
-    for (int i = 0; i < b->nq; i++) {
-        fs_result& R = results[i];
-        R.count = hr[i].count;
-        R.status = b->status[i];
-        R.pad = 0;
-        if (b->mode == FS_BATCH_LENGTHS && R.count > 0) {
-            R.min_len = (uint32_t)(0xffffffffu - hr[i].minc);
-            R.max_len = (uint32_t)hr[i].max;
-        } else {
-            R.min_len = R.max_len = 0;
-        }
-    }
-    return FS_OK;
+    return fs_batch_collect(b, results);
 }
 
 fs_status fs_batch_destroy(fs_batch* b)
 {
     if (!b) return FS_OK;
     std::lock_guard<std::mutex> lk(g_mu);
-    cudaError_t e = cudaFree(b->mem);
-    delete b;
+    cudaError_t e = cudaDeviceSynchronize();
+    batch_free(b);
     if (e != cudaSuccess) return cuda_fail(e, "batch free");
     return FS_OK;
 }

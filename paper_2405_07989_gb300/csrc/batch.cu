@@ -13,24 +13,42 @@
 
 namespace fsi {
 
+// The query a work item walks: q, or for TRIPLE queries q with one prefix
+// level fewer (the last three levels then come from the tables).
+FS_D void batch_walk_query(const BatchQ& B, QueryConst& out)
+{
+    out = B.q;
+    if (B.triple) reduce_to_triple(out);
+}
+
 __global__ void __launch_bounds__(256) k_batch_tables(BatchDev b)
 {
     __shared__ uint64_t part[256];
+    __shared__ int32_t part32[256];
+    __shared__ QueryConst qw;
     BatchQ& B = b.qs[blockIdx.x];
     if (!B.valid) return;
-    const QueryConst& q = B.q;
-    int8_t* E = q.tab_e ? (int8_t*)(b.arena + B.off_E) : nullptr;
-    int32_t* X0 = (b.mode && q.tab_xy) ? (int32_t*)(b.arena + B.off_X0) : nullptr;
-    int32_t* YD = (b.mode && q.tab_xy) ? (int32_t*)(b.arena + B.off_YD) : nullptr;
-    if (E || X0) pair_tables_fill(q, E, X0, YD, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) batch_walk_query(B, qw);
+    __syncthreads();
+    if (B.triple) {
+        triple_tables_block(B.q, (uint64_t*)(b.arena + B.off_T3),
+                            b.mode ? (int32_t*)(b.arena + B.off_MN3) : nullptr,
+                            b.mode ? (int32_t*)(b.arena + B.off_MX3) : nullptr, part, part32);
+    } else {
+        const QueryConst& q = B.q;
+        int8_t* E = q.tab_e ? (int8_t*)(b.arena + B.off_E) : nullptr;
+        int32_t* X0 = (b.mode && q.tab_xy) ? (int32_t*)(b.arena + B.off_X0) : nullptr;
+        int32_t* YD = (b.mode && q.tab_xy) ? (int32_t*)(b.arena + B.off_YD) : nullptr;
+        if (E || X0) pair_tables_fill(q, E, X0, YD, threadIdx.x, blockDim.x);
+    }
     uint64_t* W = (uint64_t*)(b.arena + B.off_W);
-    const int len = q.n + 1;
-    for (int k = q.P - 2; k >= 0; k--) {
-        const uint64_t* in = (k == q.P - 2) ? nullptr : W + (size_t)(k + 1) * len;
-        block_strided_prefix_sum(in, q.dv_in, W + (size_t)k * len, len, q.h[k], part);
+    const int len = qw.n + 1;
+    for (int k = qw.P - 2; k >= 0; k--) {
+        const uint64_t* in = (k == qw.P - 2) ? nullptr : W + (size_t)(k + 1) * len;
+        block_strided_prefix_sum(in, qw.dv_in, W + (size_t)k * len, len, qw.h[k], part);
     }
     __syncthreads();
-    if (threadIdx.x == 0) B.L = total_leaves(q, W);
+    if (threadIdx.x == 0) B.L = total_leaves(qw, W);
 }
 
 // target = max(min_leaves, ceil(sum L / items_target)); S_q = ceil(L_q / target);
@@ -98,20 +116,29 @@ FS_D int batch_query_of(const BatchDev& b, uint64_t it)
 
 __global__ void __launch_bounds__(256) k_batch_starts(BatchDev b)
 {
+    __shared__ QueryConst qs[8];
     const int lane = threadIdx.x & 31;
+    QueryConst& qw = qs[threadIdx.x >> 5];
     const uint64_t items = b.ctr[BCTR_ITEMS];
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    int cur = -1;
     for (uint64_t it = gw; it < items; it += nw) {
         const int j = batch_query_of(b, it);
         const BatchQ& B = b.qs[j];
+        if (j != cur) {
+            __syncwarp();
+            if (lane == 0) batch_walk_query(B, qw);
+            __syncwarp();
+            cur = j;
+        }
         const uint64_t s = it - B.item0;
         const uint64_t k0 = slice_start(s, B.L, B.S);
         RunPrefix rp;
-        const int32_t bb = warp_unrank(B.q, B.q.h, B.q.dv_h, (const uint64_t*)(b.arena + B.off_W),
+        const int32_t bb = warp_unrank(qw, qw.h, qw.dv_h, (const uint64_t*)(b.arena + B.off_W),
                                        k0, lane, rp);
         int32_t* st = b.starts + it * START_W;
-        if (lane < B.q.P - 1) st[lane] = rp.a;
+        if (lane < qw.P - 1) st[lane] = rp.a;
         if (lane == 0) {
             st[START_W - 3] = (int32_t)s;
             st[START_W - 2] = j;
@@ -126,6 +153,10 @@ struct BatchCons {
     const int8_t* E;
     const int32_t* X0;
     const int32_t* YD;
+    const uint64_t* T3;   // TRIPLE query: the trailing-three tables
+    const int32_t* MN3;
+    const int32_t* MX3;
+    int triple;
     PairC pc;
     int tab;  // table path usable for this query and mode
     uint64_t cnt;
@@ -140,6 +171,15 @@ struct BatchCons {
     FS_D bool chunk(const QueryConst&, int, bool valid, int32_t r, int32_t a, int32_t lp)
     {
         if (!valid) return false;
+        if (triple) {
+            const uint64_t c = __ldg(&T3[r]);
+            cnt += c;
+            if (MODE && c) {
+                mn = min(mn, (uint32_t)(lp + a + __ldg(&MN3[r])));
+                mx = max(mx, (uint32_t)(lp + a + __ldg(&MX3[r])));
+            }
+            return false;
+        }
         if (MODE == 0) {
             cnt += tab ? pair_count<true>(pc, E, r) : pair_count<false>(pc, E, r);
         } else {
@@ -186,12 +226,19 @@ __global__ void __launch_bounds__(256) k_batch_walk(BatchDev b)
             for (int w = lane; w < (int)(sizeof(QueryConst) / 4); w += 32) dst[w] = src[w];
             __syncwarp();
             cur = j;
+            cons.pc = pair_consts(q);
+            cons.tab = MODE == 0 ? q.tab_e : q.tab_xy;
+            cons.triple = B.triple;
+            __syncwarp();
+            if (B.triple && lane == 0) reduce_to_triple(q);
+            __syncwarp();
             hk = lane < q.P - 1 ? q.h[lane] : 0;
             cons.E = (const int8_t*)(b.arena + B.off_E);
             cons.X0 = (const int32_t*)(b.arena + B.off_X0);
             cons.YD = (const int32_t*)(b.arena + B.off_YD);
-            cons.pc = pair_consts(q);
-            cons.tab = MODE == 0 ? q.tab_e : q.tab_xy;
+            cons.T3 = (const uint64_t*)(b.arena + B.off_T3);
+            cons.MN3 = (const int32_t*)(b.arena + B.off_MN3);
+            cons.MX3 = (const int32_t*)(b.arena + B.off_MX3);
         }
         cons.cnt = 0;
         cons.mn = 0xffffffffu;

@@ -141,32 +141,7 @@ __global__ void __launch_bounds__(1024) k_triple_tables(const __grid_constant__ 
 {
     __shared__ uint64_t part64[1024];
     __shared__ int32_t part32[1024];
-    const int len = q.n + 1;
-    const int h = q.h[q.P - 1];
-    const Div32 dvh = q.dv_h[q.P - 1];
-    for (int p = threadIdx.x; p < len; p += blockDim.x) {
-        int32_t x0 = 0, y0 = 0;
-        const uint32_t c = pair_xy<false>(q, nullptr, nullptr, p, x0, y0);
-        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-        T3[p] = c;
-        if (c > 0) {
-            const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
-            MN3[p] = min(l0, l1) - t;
-            MX3[p] = max(l0, l1) - t;
-        } else {
-            MN3[p] = TRIPLE_NONE - t;
-            MX3[p] = -TRIPLE_NONE - t;
-        }
-    }
-    __syncthreads();
-    block_strided_scan<uint64_t>(T3, len, h, part64, (uint64_t)0, OpAdd());
-    block_strided_scan<int32_t>(MN3, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
-    block_strided_scan<int32_t>(MX3, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
-    for (int p = threadIdx.x; p < len; p += blockDim.x) {
-        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-        MN3[p] += t;
-        MX3[p] += t;
-    }
+    triple_tables_block(q, T3, MN3, MX3, part64, part32);
 }
 
 cudaError_t launch_triple_tables(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,

@@ -548,6 +548,56 @@ FS_D PairC pair_consts(const QueryConst& q)
     return p;
 }
 
+// The trailing-three tables of q for p = 0..n, built by the calling block (any
+// size; part64 / part32 hold blockDim.x entries).  See k_triple_tables.
+FS_D void triple_tables_block(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,
+                              uint64_t* part64, int32_t* part32)
+{
+    const int len = q.n + 1;
+    const int h = q.h[q.P - 1];
+    const Div32 dvh = q.dv_h[q.P - 1];
+    for (int p = threadIdx.x; p < len; p += blockDim.x) {
+        int32_t x0 = 0, y0 = 0;
+        const uint32_t c = pair_xy<false>(q, (const int32_t*)nullptr, (const int32_t*)nullptr, p, x0, y0);
+        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
+        T3[p] = c;
+        if (MN3) {
+            if (c > 0) {
+                const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
+                MN3[p] = min(l0, l1) - t;
+                MX3[p] = max(l0, l1) - t;
+            } else {
+                MN3[p] = TRIPLE_NONE - t;
+                MX3[p] = -TRIPLE_NONE - t;
+            }
+        }
+    }
+    __syncthreads();
+    block_strided_scan<uint64_t>(T3, len, h, part64, (uint64_t)0, OpAdd());
+    if (MN3) {
+        block_strided_scan<int32_t>(MN3, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
+        block_strided_scan<int32_t>(MX3, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+        for (int p = threadIdx.x; p < len; p += blockDim.x) {
+            const int32_t t = (int32_t)div32((uint32_t)p, dvh);
+            MN3[p] += t;
+            MX3[p] += t;
+        }
+    }
+    __syncthreads();
+}
+
+// The query the TRIPLE walk runs over: one prefix level fewer (in place).
+FS_HD void reduce_to_triple(QueryConst& r)
+{
+    r.D -= 1;
+    r.P -= 1;
+    r.dv_in = r.dv_h[r.P - 1];
+    r.nw = r.P - 1;
+    r.tab_e = 0;
+    r.tab_xy = 0;
+    r.lcm = 0;
+}
+
 // warp sums
 FS_D uint64_t warp_sum_u64(uint64_t v)
 {

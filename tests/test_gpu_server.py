@@ -1,0 +1,150 @@
+"""The serving loop (fs_server_*): every response equals the oracle and the
+single-query call made alone, whether the request ran alone or inside a mix
+of counts, length statistics and enumerations arriving while other batches
+are on the GPU; enumerations are admitted by their exact output bytes."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2405_07989_gb300 as fs
+from paper_2405_07989_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fs.lib()
+
+
+class _DevRows:
+    """A device address seen as a tensor (no copy), through the CUDA array interface."""
+
+    def __init__(self, ptr, rows, d, elem_bytes):
+        self.__cuda_array_interface__ = {
+            "shape": (rows, d), "typestr": "<i2" if elem_bytes == 2 else "<i4",
+            "data": (ptr, False), "version": 3, "strides": None}
+
+
+def rows_of(resp, d, elem_bytes):
+    if resp["count"] == 0:
+        return np.zeros((0, d), dtype=np.int64)
+    t = torch.as_tensor(_DevRows(resp["rows"], resp["count"], d, elem_bytes), device="cuda")
+    return t.cpu().numpy().astype(np.int64)
+
+
+def alone(op, n, g, elem_bytes=2, keep_order=False):
+    """The same request through the single-query entry points."""
+    cfg = fs.make_config(keep_order=keep_order)
+    if op == fs.REQ_COUNT:
+        return (fs.fs_count(n, g),)
+    if op == fs.REQ_LENGTHS:
+        return fs.fs_length_stats(n, g)
+    c = fs.fs_count(n, g)
+    dt = torch.int16 if elem_bytes == 2 else torch.int32
+    out = torch.empty((max(c, 1), len(g)), dtype=dt, device="cuda")
+    fs.fs_enumerate(n, g, out, cap=c, elem_bytes=elem_bytes, cfg=cfg)
+    return out[:c].cpu().numpy().astype(np.int64)
+
+
+def drain(srv, tickets, timeout_s=120.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < len(tickets):
+        for r in srv.poll(256, wait_ms=50):
+            got[r["ticket"]] = r
+        assert time.time() - t0 < timeout_s, f"{len(got)} of {len(tickets)} responses"
+    return got
+
+
+def check(resp, op, n, g, elem_bytes=2, keep_order=False):
+    assert resp["status"] == fs.FS_OK, resp
+    c = oracle.count_dp(n, g)
+    assert resp["count"] == c
+    if op in (fs.REQ_LENGTHS, fs.REQ_ENUMERATE) and c > 0:
+        assert (resp["min_len"], resp["max_len"]) == oracle.minmax_dp(n, g)
+    ref = alone(op, n, g, elem_bytes, keep_order)
+    if op == fs.REQ_COUNT:
+        assert (resp["count"],) == ref
+    elif op == fs.REQ_LENGTHS:
+        assert (resp["count"], resp["min_len"], resp["max_len"]) == ref
+    else:
+        rows = rows_of(resp, len(g), elem_bytes)
+        assert np.array_equal(rows, ref)  # byte-identical to the call alone
+        if c <= 200000:  # and the same set as the oracle's
+            srt = rows[np.lexsort(rows.T[::-1])] if c else rows
+            assert np.array_equal(srt, oracle.enumerate_sorted(n, g).astype(np.int64).reshape(-1, len(g)))
+
+
+def test_server_mix_matches_alone():
+    """A config-5-like mix (80 % count, 15 % lengths, 5 % enumerate), submitted
+    in bursts while earlier batches run."""
+    reqs = workloads.config5(seed=4, nreq=240, n_max=2500)
+    with fs.Server(mem_budget_bytes=512 << 20, max_batch=64, slots=3, window_us=100) as srv:
+        tickets = {}
+        for i, (_, op, n, g) in enumerate(reqs):
+            tickets[srv.submit(op, n, g, elem_bytes=2)] = (op, n, g)
+            if i % 40 == 39:
+                time.sleep(0.002)
+        got = drain(srv, tickets)
+        for t, (op, n, g) in tickets.items():
+            check(got[t], op, n, g)
+            assert got[t]["t_submit"] <= got[t]["t_start"] <= got[t]["t_done"]
+            if op == fs.REQ_ENUMERATE:
+                srv.release(t)
+
+
+@pytest.mark.parametrize("op", [fs.REQ_COUNT, fs.REQ_LENGTHS, fs.REQ_ENUMERATE])
+def test_server_request_alone(op):
+    n, g = 2000, (11, 13, 17, 19, 23)
+    with fs.Server(mem_budget_bytes=64 << 20) as srv:
+        t = srv.submit(op, n, g, elem_bytes=4, keep_order=True)
+        got = drain(srv, {t: None})
+        check(got[t], op, n, g, elem_bytes=4, keep_order=True)
+
+
+def test_server_invalid_and_capacity():
+    n_big, g_big = 3000, (11, 13, 17, 19, 23, 29)  # 72 082 790 rows: 865 MB of int16
+    with fs.Server(mem_budget_bytes=8 << 20, max_batch=16) as srv:
+        ts = [srv.submit(fs.REQ_COUNT, 100, (3, 0, 7)),
+              srv.submit(fs.REQ_ENUMERATE, n_big, g_big, elem_bytes=2),
+              srv.submit(fs.REQ_LENGTHS, 700, (5, 7, 11, 13)),
+              srv.submit(fs.REQ_ENUMERATE, 40000, (1, 2), elem_bytes=2)]  # a_1 up to 40000: no int16
+        got = drain(srv, ts)
+        assert got[ts[0]]["status"] == fs.FS_E_INVAL
+        assert got[ts[1]]["status"] == fs.FS_E_CAPACITY
+        assert got[ts[1]]["count"] == oracle.count_dp(n_big, g_big)
+        check(got[ts[2]], fs.REQ_LENGTHS, 700, (5, 7, 11, 13))
+        assert got[ts[3]]["status"] == fs.FS_E_OVERFLOW
+        with pytest.raises(fs.FsError):
+            srv.submit(7, 100, (3, 5))
+        with pytest.raises(fs.FsError):
+            srv.submit(fs.REQ_ENUMERATE, 100, (3, 5), elem_bytes=8)
+
+
+def test_server_enumerate_waits_for_release():
+    """Two enumerations that do not fit the budget together: the second is
+    materialised only after the first one's rows are released."""
+    n, g = 1500, (7, 9, 11, 13)
+    c = oracle.count_dp(n, g)
+    need = c * len(g) * 2
+    with fs.Server(mem_budget_bytes=need + need // 2, max_batch=8) as srv:
+        a = srv.submit(fs.REQ_ENUMERATE, n, g)
+        b = srv.submit(fs.REQ_ENUMERATE, n, g)
+        first = drain(srv, [a])
+        assert first[a]["status"] == fs.FS_OK
+        time.sleep(0.3)
+        assert srv.poll(8, wait_ms=100) == []  # b waits for room
+        ra = rows_of(first[a], len(g), 2)
+        srv.release(a)
+        second = drain(srv, [b])
+        check(second[b], fs.REQ_ENUMERATE, n, g)
+        assert np.array_equal(rows_of(second[b], len(g), 2), ra)
+        srv.release(b)
+        with pytest.raises(fs.FsError):
+            srv.release(b)
