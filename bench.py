@@ -386,8 +386,9 @@ def heavy_count_extras(fs, workloads, dev):
         return int(dc[0].item()), ms, prof.get(walk, (1, ms))[1], prof
 
     Z, ms, walk_ms, _ = timed_count(pair, "pair_count")
-    Z3, ms3, walk3, prof3 = timed_count(None, "triple_count")
-    assert Z3 == Z
+    Z3, ms3, walk3, prof3 = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count")
+    Z4, ms4, walk4, prof4 = timed_count(None, "quad_count")
+    assert Z3 == Z and Z4 == Z
     achieved = leaves * COUNT_OPS_PER_LEAF / (walk_ms / 1000.0)
     hist = torch.zeros(n // min(g) + 1, dtype=torch.int64, device=dev)
     t0 = time.perf_counter()
@@ -404,6 +405,9 @@ def heavy_count_extras(fs, workloads, dev):
         "count_triple_ms": ms3, "count_triple_walk_ms": walk3,
         "count_triple_factorizations_per_s": Z / (ms3 / 1000.0),
         "count_triple_breakdown_ms": {k: v[1] for k, v in prof3.items()},
+        "count_quad_ms": ms4, "count_quad_walk_ms": walk4,
+        "count_quad_factorizations_per_s": Z / (ms4 / 1000.0),
+        "count_quad_breakdown_ms": {k: v[1] for k, v in prof4.items()},
         "count_roofline": {"bound": "alu", "achieved": achieved, "peak": rates["add"],
                            "unit": "int32 lane-ops/s", "frac": achieved / rates["add"],
                            "ops_per_leaf": COUNT_OPS_PER_LEAF, "peak_source": "probed add rate"},

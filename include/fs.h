@@ -77,11 +77,16 @@ typedef enum fs_method {
      * coordinates.  Count and min / max length only (fs_count, fs_length_stats
      * without a histogram, fs_slice_counts); needs d >= 4.  AUTO uses it for
      * those when it applies, PAIR otherwise. */
-    FS_METHOD_TRIPLE = 3
+    FS_METHOD_TRIPLE = 3,
+    /* QUAD: the same with tables over the last four coordinates (each table
+     * entry one more strided sum of the trailing-three table), so the walk
+     * visits only the prefixes of the first d-4; needs d >= 5 and n < 2^22.
+     * AUTO prefers it to TRIPLE where it applies. */
+    FS_METHOD_QUAD = 4
 } fs_method;
 
 typedef struct fs_config {
-    int32_t method;        /* fs_method; AUTO = TRIPLE where it applies, else PAIR */
+    int32_t method;        /* fs_method; AUTO = QUAD, else TRIPLE where they apply, else PAIR */
     int32_t keep_order;    /* 1: walk the generators in the caller's order.  0 (default):
                               walk them in descending order, which visits the fewest
                               prefixes; the result is the same set (Z does not depend on

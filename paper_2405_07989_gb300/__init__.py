@@ -19,7 +19,7 @@ MAX_D = 16
 
 FS_OK, FS_E_INVAL, FS_E_OVERFLOW, FS_E_CAPACITY = 0, 1, 2, 3
 FS_E_NOMEM, FS_E_CUDA, FS_E_TIMEOUT, FS_E_NOTIMPL = 4, 5, 6, 7
-METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR, METHOD_TRIPLE = 0, 1, 2, 3
+METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR, METHOD_TRIPLE, METHOD_QUAD = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()
 _lib = None

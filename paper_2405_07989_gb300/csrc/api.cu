@@ -275,12 +275,26 @@ int method_of(const fs_config& c)
     return c.method == FS_METHOD_PLAIN ? FS_METHOD_PLAIN : FS_METHOD_PAIR;
 }
 
-// The query the TRIPLE walk runs over: the first D-3 levels as prefix levels
-// (one fewer than PAIR); the last three come from the trailing tables.
-QueryConst reduce_triple(const QueryConst& q)
+// The query the trailing-k walk runs over: the first D-k levels as prefix
+// levels (k - 2 fewer than PAIR); the last k come from the trailing tables.
+// Trailing levels the tables can take for q under `method` (0: none).
+// k = 3 needs D >= 4 (one prefix level left) and n < 2^27 (the length
+// sentinels stay in int32); k = 4 needs D >= 5 and n < 2^22, so that a table
+// entry, at most C(n + 3, 3) < 2^64, cannot overflow.  AUTO and QUAD take
+// the deepest that applies; TRIPLE takes 3.
+int trailing_levels(const QueryConst& q, int method)
+{
+    const bool k4 = q.D >= 5 && q.n < (1 << 22);
+    const bool k3 = q.D >= 4 && q.n < (1 << 27);
+    if (method == FS_METHOD_TRIPLE) return k3 ? 3 : 0;
+    if (method == FS_METHOD_QUAD) return k4 ? 4 : 0;
+    return k4 ? 4 : k3 ? 3 : 0;
+}
+
+QueryConst reduce_trailing(const QueryConst& q, int k)
 {
     QueryConst r = q;
-    reduce_to_triple(r);
+    reduce_to_trailing(r, k);
     return r;
 }
 
@@ -394,7 +408,11 @@ const char* walk_name(Op op, int method)
     static const char* plain[] = {"plain_count", "plain_slice_count", "plain_len", "plain_any",
                                   "plain_enum"};
     static const char* triple[] = {"triple_count", "triple_slice_count", "triple_len", "", ""};
-    return method == FS_METHOD_PLAIN ? plain[op] : method == FS_METHOD_TRIPLE ? triple[op] : pair[op];
+    static const char* quad[] = {"quad_count", "quad_slice_count", "quad_len", "", ""};
+    return method == FS_METHOD_PLAIN    ? plain[op]
+           : method == FS_METHOD_TRIPLE ? triple[op]
+           : method == FS_METHOD_QUAD   ? quad[op]
+                                        : pair[op];
 }
 
 cudaError_t launch_walk(const QueryConst& q, const Scratch& sc, Op op, int method, const LaunchCfg& lc,
@@ -409,9 +427,10 @@ cudaError_t launch_walk(const QueryConst& q, const Scratch& sc, Op op, int metho
 // Everything a call enqueues: precompute, walk(s), finalisation.
 struct Call {
     Query Q;
-    QueryConst q3;  // TRIPLE: the reduced query the walk runs over
+    QueryConst q3;  // trailing tables: the reduced query the walk runs over
     fs_config cfg;
-    int method = FS_METHOD_PAIR;
+    int method = FS_METHOD_PAIR;  // PLAIN, PAIR, or TRIPLE for the trailing-k tables
+    int trail = 0;                // TRIPLE: k = 3 or 4 trailing levels in the tables
     DevState* ds = nullptr;
     Scratch sc;
     Layout L;
@@ -431,22 +450,29 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
     c.st = (cudaStream_t)stream;
     fs_status s = build_query(n, gens, d, c.cfg, c.Q);
     if (s != FS_OK) return s;
-    const bool tri_ok = c.Q.q.D >= 4 && c.Q.q.n < (1 << 27) &&
-                        (op == OP_COUNT || op == OP_SLICES || (op == OP_LEN && lengths_only));
+    if (c.cfg.method < FS_METHOD_AUTO || c.cfg.method > FS_METHOD_QUAD)
+        return fail(FS_E_INVAL, "method %d", c.cfg.method);
+    const bool op_ok = op == OP_COUNT || op == OP_SLICES || (op == OP_LEN && lengths_only);
+    const int kmax = trailing_levels(c.Q.q, FS_METHOD_AUTO);
     if (c.cfg.method == FS_METHOD_PLAIN) {
         c.method = FS_METHOD_PLAIN;
-    } else if (c.cfg.method == FS_METHOD_TRIPLE) {
-        if (!tri_ok)
-            return fail(FS_E_NOTIMPL, "TRIPLE serves count / slice counts / min-max lengths with "
-                                      "d >= 4 and n < 2^27 only");
+    } else if (c.cfg.method == FS_METHOD_TRIPLE || c.cfg.method == FS_METHOD_QUAD) {
+        c.trail = trailing_levels(c.Q.q, c.cfg.method);
+        if (!op_ok || c.trail == 0)
+            return fail(FS_E_NOTIMPL, "%s serves count / slice counts / min-max lengths with "
+                                      "d >= %d and n < 2^%d only",
+                        c.cfg.method == FS_METHOD_TRIPLE ? "TRIPLE" : "QUAD",
+                        c.cfg.method == FS_METHOD_TRIPLE ? 4 : 5,
+                        c.cfg.method == FS_METHOD_TRIPLE ? 27 : 22);
         c.method = FS_METHOD_TRIPLE;
-    } else if (c.cfg.method == FS_METHOD_AUTO && tri_ok) {
+    } else if (c.cfg.method == FS_METHOD_AUTO && op_ok && kmax > 0) {
+        c.trail = kmax;
         c.method = FS_METHOD_TRIPLE;
     } else {
         c.method = FS_METHOD_PAIR;
     }
     const bool triple = c.method == FS_METHOD_TRIPLE;
-    if (triple) c.q3 = reduce_triple(c.Q.q);
+    if (triple) c.q3 = reduce_trailing(c.Q.q, c.trail);
     const QueryConst& qw = c.wq();
     s = get_dev(&c.ds);
     if (s != FS_OK) return s;
@@ -471,7 +497,8 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
         ProfScope ps("precompute", c.st,
                      ((qw.tab_e || qw.tab_xy) ? 1 : 0) + (qw.nw > 0 ? 1 : 0) + (triple ? 1 : 0));
         e = launch_precompute(qw, c.sc, c.st);
-        if (e == cudaSuccess && triple) e = launch_triple_tables(c.Q.q, c.T3, c.MN3, c.MX3, c.st);
+        if (e == cudaSuccess && triple)
+            e = launch_trailing_tables(c.Q.q, c.trail, c.T3, c.MN3, c.MX3, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
     {
@@ -498,7 +525,7 @@ cudaError_t call_walk(Call& c, Op op, int queue, const PredConst* pred, void* ou
                       int eb)
 {
     if (c.method == FS_METHOD_TRIPLE) {
-        ProfScope ps(walk_name(op, c.method), c.st, 1);
+        ProfScope ps(walk_name(op, c.trail == 4 ? FS_METHOD_QUAD : FS_METHOD_TRIPLE), c.st, 1);
         return launch_triple(c.q3, c.sc, op, c.lc, queue, c.T3, c.MN3, c.MX3, c.st);
     }
     return launch_walk(c.Q.q, c.sc, op, c.method, c.lc, queue, pred, out, cap, eb, c.st);
@@ -913,11 +940,11 @@ uint64_t batch_plan_host(const fs_query* queries, int nq, int mode, const fs_con
         if (s != FS_OK) continue;
         B.q = qq.q;
         B.valid = 1;
-        // the trailing-three tables unless PAIR is asked for
-        B.triple = cc.method != FS_METHOD_PAIR && B.q.D >= 4 && B.q.n < (1 << 27);
+        // the trailing tables unless PAIR is asked for
+        B.trail = cc.method == FS_METHOD_PAIR ? 0 : trailing_levels(B.q, cc.method);
         const size_t n1 = (size_t)B.q.n + 1;
-        if (B.triple) {
-            B.off_W = take((size_t)(B.q.nw - 1) * n1 * 8);
+        if (B.trail) {
+            B.off_W = take((size_t)(B.q.nw - (B.trail - 2)) * n1 * 8);
             B.off_T3 = take(n1 * 8);
             B.off_MN3 = take(mode == FS_BATCH_LENGTHS ? n1 * 4 : 0);
             B.off_MX3 = take(mode == FS_BATCH_LENGTHS ? n1 * 4 : 0);

@@ -13,12 +13,12 @@
 
 namespace fsi {
 
-// The query a work item walks: q, or for TRIPLE queries q with one prefix
-// level fewer (the last three levels then come from the tables).
+// The query a work item walks: q, or for trailing-k queries q with k - 2
+// prefix levels fewer (the last k levels then come from the tables).
 FS_D void batch_walk_query(const BatchQ& B, QueryConst& out)
 {
     out = B.q;
-    if (B.triple) reduce_to_triple(out);
+    if (B.trail) reduce_to_trailing(out, B.trail);
 }
 
 __global__ void __launch_bounds__(256) k_batch_tables(BatchDev b)
@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(256) k_batch_tables(BatchDev b)
     if (!B.valid) return;
     if (threadIdx.x == 0) batch_walk_query(B, qw);
     __syncthreads();
-    if (B.triple) {
-        triple_tables_block(B.q, (uint64_t*)(b.arena + B.off_T3),
+    if (B.trail) {
+        trailing_tables_block(B.q, B.trail, (uint64_t*)(b.arena + B.off_T3),
                             b.mode ? (int32_t*)(b.arena + B.off_MN3) : nullptr,
                             b.mode ? (int32_t*)(b.arena + B.off_MX3) : nullptr, part, part32);
     } else {
@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(256) k_batch_walk(BatchDev b)
             cur = j;
             cons.pc = pair_consts(q);
             cons.tab = MODE == 0 ? q.tab_e : q.tab_xy;
-            cons.triple = B.triple;
+            cons.triple = B.trail != 0;
             __syncwarp();
-            if (B.triple && lane == 0) reduce_to_triple(q);
+            if (B.trail && lane == 0) reduce_to_trailing(q, B.trail);
             __syncwarp();
             hk = lane < q.P - 1 ? q.h[lane] : 0;
             cons.E = (const int8_t*)(b.arena + B.off_E);

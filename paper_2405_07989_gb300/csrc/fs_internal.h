@@ -127,12 +127,12 @@ struct Scratch {
 struct BatchQ {
     QueryConst q;
     uint64_t off_W, off_E, off_X0, off_YD;  // byte offsets of its tables in the arena
-    uint64_t off_T3, off_MN3, off_MX3;      // TRIPLE tables (triple = 1)
+    uint64_t off_T3, off_MN3, off_MX3;      // trailing-k tables (trail = k)
     uint64_t L;      // leaves of the walk (device)
     uint64_t S;      // slices (device)
     uint64_t item0;  // first work item (device)
     int32_t valid;   // 0: invalid query, skipped
-    int32_t triple;  // 1: walk the first d-3 levels, the last three from tables
+    int32_t trail;   // k = 3 or 4: walk the first d-k levels, the last k from tables; 0: pair
 };
 
 struct BatchRes {

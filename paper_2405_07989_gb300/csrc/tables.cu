@@ -127,27 +127,29 @@ __global__ void __launch_bounds__(1024) k_len_finalize(const __grid_constant__ Q
 
 __global__ void k_copy_u64(const uint64_t* src, uint64_t* dst) { *dst = *src; }
 
-// Trailing-three tables (Sec. 6.1: keep the factorizations of every small
+// Trailing-k tables (Sec. 6.1: keep the factorizations of every small
 // residual over the trailing generators, here their count and length range).
-// With h = h_{P-1} and the pair (A, B) of q, for p = 0..n:
-//   T3[p]  = #{(a, x, y) >= 0 : a h + x A + y B = p} = sum_{a >= 0} c2(p - a h)
-//   MN3[p] = min of a + x + y over those solutions (TRIPLE_NONE if none)
-//   MX3[p] = max of a + x + y (-TRIPLE_NONE if none)
+// For k = 3, with h = h_{P-1} and the pair (A, B) of q, for p = 0..n:
+//   T[p]  = #{(a, x, y) >= 0 : a h + x A + y B = p} = sum_{a >= 0} c2(p - a h)
+//   MN[p] = min of a + x + y over those solutions (TRIPLE_NONE if none)
+//   MX[p] = max of a + x + y (-TRIPLE_NONE if none)
 // c2 and the pair's length range come from the pair's closed form (its lengths
 // run l0 + t delta); the sums over a are strided scans: a running sum, and a
-// running min / max of (pair bound - floor(p/h)) plus floor(p/h).  One block.
-__global__ void __launch_bounds__(1024) k_triple_tables(const __grid_constant__ QueryConst q,
-                                                        uint64_t* T3, int32_t* MN3, int32_t* MX3)
+// running min / max of (bound - floor(p/h)) plus floor(p/h).  k = 4 adds level
+// P-2 the same way: T4[p] = sum_{b >= 0} T3[p - b h_{P-2}], and so on for the
+// length range.  One block.
+__global__ void __launch_bounds__(1024) k_trailing_tables(const __grid_constant__ QueryConst q, int k,
+                                                          uint64_t* T, int32_t* MN, int32_t* MX)
 {
     __shared__ uint64_t part64[1024];
     __shared__ int32_t part32[1024];
-    triple_tables_block(q, T3, MN3, MX3, part64, part32);
+    trailing_tables_block(q, k, T, MN, MX, part64, part32);
 }
 
-cudaError_t launch_triple_tables(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,
-                                 cudaStream_t st)
+cudaError_t launch_trailing_tables(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
+                                   cudaStream_t st)
 {
-    k_triple_tables<<<1, 1024, 0, st>>>(q, T3, MN3, MX3);
+    k_trailing_tables<<<1, 1024, 0, st>>>(q, k, T, MN, MX);
     return cudaGetLastError();
 }
 

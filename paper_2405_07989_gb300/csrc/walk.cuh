@@ -548,49 +548,59 @@ FS_D PairC pair_consts(const QueryConst& q)
     return p;
 }
 
-// The trailing-three tables of q for p = 0..n, built by the calling block (any
-// size; part64 / part32 hold blockDim.x entries).  See k_triple_tables.
-FS_D void triple_tables_block(const QueryConst& q, uint64_t* T3, int32_t* MN3, int32_t* MX3,
-                              uint64_t* part64, int32_t* part32)
+// The trailing-k tables of q (k = 3 or 4) for p = 0..n, built by the calling
+// block (any size; part64 / part32 hold blockDim.x entries).  Level P-1 is
+// summed over the pair's closed form; each further level (P-2 for k = 4) is
+// one more strided scan of the same tables in place.  See k_trailing_tables.
+FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
+                                uint64_t* part64, int32_t* part32)
 {
     const int len = q.n + 1;
-    const int h = q.h[q.P - 1];
-    const Div32 dvh = q.dv_h[q.P - 1];
-    for (int p = threadIdx.x; p < len; p += blockDim.x) {
-        int32_t x0 = 0, y0 = 0;
-        const uint32_t c = pair_xy<false>(q, (const int32_t*)nullptr, (const int32_t*)nullptr, p, x0, y0);
-        const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-        T3[p] = c;
-        if (MN3) {
-            if (c > 0) {
-                const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
-                MN3[p] = min(l0, l1) - t;
-                MX3[p] = max(l0, l1) - t;
-            } else {
-                MN3[p] = TRIPLE_NONE - t;
-                MX3[p] = -TRIPLE_NONE - t;
-            }
-        }
-    }
-    __syncthreads();
-    block_strided_scan<uint64_t>(T3, len, h, part64, (uint64_t)0, OpAdd());
-    if (MN3) {
-        block_strided_scan<int32_t>(MN3, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
-        block_strided_scan<int32_t>(MX3, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+    for (int lvl = q.P - 1; lvl >= q.P + 2 - k; lvl--) {
+        const int h = q.h[lvl];
+        const Div32 dvh = q.dv_h[lvl];
         for (int p = threadIdx.x; p < len; p += blockDim.x) {
             const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-            MN3[p] += t;
-            MX3[p] += t;
+            if (lvl == q.P - 1) {
+                int32_t x0 = 0, y0 = 0;
+                const uint32_t c =
+                    pair_xy<false>(q, (const int32_t*)nullptr, (const int32_t*)nullptr, p, x0, y0);
+                T[p] = c;
+                if (MN) {
+                    if (c > 0) {
+                        const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
+                        MN[p] = min(l0, l1) - t;
+                        MX[p] = max(l0, l1) - t;
+                    } else {
+                        MN[p] = TRIPLE_NONE - t;
+                        MX[p] = -TRIPLE_NONE - t;
+                    }
+                }
+            } else if (MN) {
+                MN[p] -= t;
+                MX[p] -= t;
+            }
         }
+        __syncthreads();
+        block_strided_scan<uint64_t>(T, len, h, part64, (uint64_t)0, OpAdd());
+        if (MN) {
+            block_strided_scan<int32_t>(MN, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
+            block_strided_scan<int32_t>(MX, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+            for (int p = threadIdx.x; p < len; p += blockDim.x) {
+                const int32_t t = (int32_t)div32((uint32_t)p, dvh);
+                MN[p] += t;
+                MX[p] += t;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
-// The query the TRIPLE walk runs over: one prefix level fewer (in place).
-FS_HD void reduce_to_triple(QueryConst& r)
+// The query the trailing-k walk runs over: k - 2 prefix levels fewer (in place).
+FS_HD void reduce_to_trailing(QueryConst& r, int k)
 {
-    r.D -= 1;
-    r.P -= 1;
+    r.D -= k - 2;
+    r.P -= k - 2;
     r.dv_in = r.dv_h[r.P - 1];
     r.nw = r.P - 1;
     r.tab_e = 0;

@@ -40,6 +40,15 @@ def test_batch_small_random(mode):
     assert got == expected(qs, mode)
 
 
+@pytest.mark.parametrize("method", [fs.METHOD_PAIR, fs.METHOD_TRIPLE, fs.METHOD_QUAD])
+def test_batch_methods_agree(method):
+    """Pair walks, trailing-three and trailing-four tables give the same
+    per-query results."""
+    qs = workloads.config4(seed=13, nq=200, n_max=4000)
+    cfg = fs.make_config(method=method)
+    assert fs.fs_batch_run(qs, fs.BATCH_LENGTHS, cfg) == expected(qs, fs.BATCH_LENGTHS)
+
+
 def test_batch_invalid_queries_are_flagged_and_skipped():
     qs = [(100, (3, 5, 7)), (100, (3, 0, 7)), (-5, (2, 3)), (2**31 - 3, (5, 7, 9)),
           (200, (11, 13))]

@@ -33,6 +33,8 @@ PAIR_KEEP = fs.make_config(method=fs.METHOD_PAIR, keep_order=True)
 CONFIGS = {"pair": PAIR, "plain": PLAIN, "pair_keep": PAIR_KEEP, "plain_keep": PLAIN_KEEP}
 TRIPLE = fs.make_config(method=fs.METHOD_TRIPLE)
 TRIPLE_KEEP = fs.make_config(method=fs.METHOD_TRIPLE, keep_order=True)
+QUAD = fs.make_config(method=fs.METHOD_QUAD)
+QUAD_KEEP = fs.make_config(method=fs.METHOD_QUAD, keep_order=True)
 AUTO = fs.make_config()
 
 
@@ -77,12 +79,15 @@ def test_count_random(method):
         assert fs.fs_count(n, g, cfg) == oracle.count_dp(n, g), (n, g)
 
 
-@pytest.mark.parametrize("cfg", [TRIPLE, TRIPLE_KEEP, AUTO], ids=["triple", "triple_keep", "auto"])
+@pytest.mark.parametrize("cfg", [TRIPLE, TRIPLE_KEEP, QUAD, QUAD_KEEP, AUTO],
+                         ids=["triple", "triple_keep", "quad", "quad_keep", "auto"])
 def test_count_triple(cfg):
-    """The trailing-three tables (Sec. 6.1) give the same counts; explicit
-    TRIPLE refuses d < 4, AUTO falls back to PAIR there."""
+    """The trailing-three and trailing-four tables (Sec. 6.1) give the same
+    counts; explicit TRIPLE refuses d < 4, QUAD d < 5, AUTO falls back to the
+    shallower tables or PAIR there."""
+    dmin = 5 if cfg in (QUAD, QUAD_KEEP) else 4
     for n, g in medium_cases():
-        if len(g) < 4 and cfg is not AUTO:
+        if len(g) < dmin and cfg is not AUTO:
             with pytest.raises(fs.FsError) as e:
                 fs.fs_count(n, g, cfg)
             assert e.value.status == fs.FS_E_NOTIMPL
@@ -98,6 +103,8 @@ def test_length_min_max_triple():
         assert fs.fs_length_stats(n, g, None, AUTO) == expect, (n, g)
         if len(g) >= 4:
             assert fs.fs_length_stats(n, g, None, TRIPLE) == expect, (n, g)
+        if len(g) >= 5:
+            assert fs.fs_length_stats(n, g, None, QUAD) == expect, (n, g)
     with pytest.raises(fs.FsError) as e:  # a histogram needs the PAIR walk
         h = torch.zeros(1000, dtype=torch.int64, device="cuda")
         fs.fs_length_stats(300, (11, 13, 17, 19), h, TRIPLE)
@@ -348,13 +355,20 @@ def test_plan_and_slice_counts_match_oracle(slices):
             assert len(live) == slices
 
 
+@pytest.mark.parametrize("k", [3, 4])
 @pytest.mark.parametrize("slices", [1, 3, 64, 2000])
-def test_triple_slices_match_oracle(slices):
-    """TRIPLE slices cut the prefixes one level shorter; each slice still holds
-    exactly what the oracle's bounded stream finds between its bounds."""
-    for n, g in [(600, (13, 37, 38, 40)), (250, (11, 13, 17, 19, 23)), workloads.CONFIG1]:
-        order, bounds, leaves = fs.fs_plan(n, g, slices, TRIPLE)
-        counts = fs.fs_slice_counts(n, g, slices, TRIPLE)
+def test_triple_slices_match_oracle(slices, k):
+    """Trailing-k slices cut the prefixes k - 2 levels shorter; each slice
+    still holds exactly what the oracle's bounded stream finds between its
+    bounds."""
+    cfg = TRIPLE if k == 3 else QUAD
+    cases = [(600, (13, 37, 38, 40)), (250, (11, 13, 17, 19, 23)), workloads.CONFIG1,
+             (700, (5, 7, 9, 11, 13, 15))]
+    for n, g in cases:
+        if len(g) < k + 1:
+            continue
+        order, bounds, leaves = fs.fs_plan(n, g, slices, cfg)
+        counts = fs.fs_slice_counts(n, g, slices, cfg)
         wg = walk_gens(g, order)
         total = 0
         for s_ in range(slices):
@@ -362,7 +376,7 @@ def test_triple_slices_match_oracle(slices):
             if lo[0] < 0:
                 assert counts[s_] == 0
                 continue
-            assert lo[-1] == 0 and lo[-2] == 0 and lo[-3] == 0
+            assert all(x == 0 for x in lo[-k:])
             hi = bounds[s_ + 1] if bounds[s_ + 1][0] >= 0 else None
             c, _, _, _, _ = oracle.range_stats(n, wg, lo, hi, with_hist=False)
             assert counts[s_] == c, (n, g, s_)
@@ -456,7 +470,10 @@ def test_config3_count_and_lengths_dp_exact():
     assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref)
     assert (mn, mx) == oracle.minmax_dp(n, g)
     assert fs.fs_count(n, g, PAIR) == expect
+    assert fs.fs_count(n, g, TRIPLE) == expect
+    assert fs.fs_count(n, g, QUAD) == expect
     assert fs.fs_length_stats(n, g, None) == (expect,) + oracle.minmax_dp(n, g)
+    assert fs.fs_length_stats(n, g, None, TRIPLE) == (expect,) + oracle.minmax_dp(n, g)
     S = 1 << 20
     order, bounds, leaves = fs.fs_plan(n, g, S, PAIR)
     counts = fs.fs_slice_counts(n, g, S, PAIR)
@@ -474,3 +491,4 @@ def test_config3_other_seeds(seed):
     n, g = workloads.config3(seed)
     assert fs.fs_count(n, g) == oracle.count_dp(n, g)
     assert fs.fs_count(n, g, PAIR) == oracle.count_dp(n, g)
+    assert fs.fs_count(n, g, TRIPLE) == oracle.count_dp(n, g)
