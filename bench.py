@@ -140,6 +140,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over all ranks (the job takes as long as its slowest
+    replica); x itself when there is one rank."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: int, ws: int, ms: float) -> float:
+    """Whole-job throughput of ws independent replicas that each process
+    units_per_rank units, given the max-over-ranks time in ms."""
+    return ws * units_per_rank / (ms / 1000.0)
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline / reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -276,13 +294,9 @@ def run_gpu(args):
         dist.barrier()
     clk = clocks.stop()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(ms_steps) / len(ms_steps)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(ms_steps) / len(ms_steps), ws, dev)
     assert int(dc[0]) == Z and int(dc[1]) == Z
-    value = ws * Z / (ms / 1000.0)
+    value = replica_value(Z, ws, ms)
     launches = sum(v[0] for v in prof.values()) // args.steps
 
     # ---- roofline of the dominant kernel (enumerate write walk) ----
@@ -310,8 +324,8 @@ def run_gpu(args):
         host.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
         assert c1 == Z and c2 == Z
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ws * Z / e2e_s, "unit": "factorizations/s",
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws, dev)
+    e2e = {"value": replica_value(Z, ws, e2e_s * 1000.0), "unit": "factorizations/s",
            "h2d_bytes_per_step": 2 * d * 4,
            "d2h_bytes_per_step": Z * row_bytes + 2 * 8 * 16,
            "ms_per_step": e2e_s * 1000.0}
@@ -532,16 +546,27 @@ def serving_extras(fs, workloads, rate: float, nreq: int):
 def run_profile_case(args):
     """Small cases of the same kernels for ncu captures, a few calls each:
     "enum": the single-large-query generators at a smaller n (output still
-    larger than L2); "count": the heavy count-only query's generators at a
-    smaller n (same run structure, milliseconds instead of seconds)."""
+    larger than L2); "count" / "count_triple" / "count_quad": the heavy
+    count-only query's generators at --profile-n through the PAIR walk or the
+    trailing-three / trailing-four tables; "batch": the first --profile-n
+    queries of the batched workload, count mode."""
     import torch
     import paper_2405_07989_gb300 as fs
     from paper_2405_07989_gb300 import workloads
-    if args.profile_case in ("count", "count_triple"):
+    if args.profile_case == "batch":
+        qs = workloads.config4(0, nq=args.profile_n)
+        with fs.Batch(qs, fs.BATCH_COUNT) as b:
+            for _ in range(args.steps):
+                b.launch()
+            res = b.results()
+        print(json.dumps({"profile_case": {"queries": len(qs), "calls": args.steps,
+                                           "factorizations": sum(r[0] for r in res)}}))
+        return 0
+    if args.profile_case in ("count", "count_triple", "count_quad"):
         n, g = workloads.config3(0, n=args.profile_n)
         dc = torch.zeros(1, dtype=torch.int64, device="cuda")
-        cfg = fs.make_config(method=fs.METHOD_PAIR if args.profile_case == "count"
-                             else fs.METHOD_TRIPLE)
+        cfg = fs.make_config(method={"count": fs.METHOD_PAIR, "count_triple": fs.METHOD_TRIPLE,
+                                     "count_quad": fs.METHOD_QUAD}[args.profile_case])
         for _ in range(args.steps):
             fs.fs_count_async(n, g, dc, cfg)
         torch.cuda.synchronize()
@@ -573,7 +598,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the heavy count-only query measurements")
-    ap.add_argument("--profile-case", choices=["enum", "count", "count_triple"], default=None,
+    ap.add_argument("--profile-case", choices=["enum", "count", "count_triple", "count_quad", "batch"],
+                    default=None,
                     help="run only a small case of the same kernels (for ncu)")
     ap.add_argument("--profile-n", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=1000.0,

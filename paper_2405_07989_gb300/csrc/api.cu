@@ -1169,7 +1169,7 @@ fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int threads_c[] = {128, 256};
-    const int per_warp_c[] = {2, 8, 32};
+    const int per_warp_c[] = {2, 4, 8, 16, 32};
     double best_t = 1e30;
     fs_config bc;
     memset(&bc, 0, sizeof bc);
@@ -1185,17 +1185,19 @@ fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config
             if (s != FS_OK) break;
             s = fs_batch_launch(b, st);  // warm-up
             if (s != FS_OK) break;
-            cudaEventRecord(e0, st);
-            s = fs_batch_launch(b, st);
-            cudaEventRecord(e1, st);
-            if (s != FS_OK) break;
-            cudaError_t e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                s = cuda_fail(e, "autotune timing");
-                break;
+            float ms = 1e30f;  // best of three
+            for (int rep = 0; rep < 3 && s == FS_OK; rep++) {
+                cudaEventRecord(e0, st);
+                s = fs_batch_launch(b, st);
+                cudaEventRecord(e1, st);
+                if (s != FS_OK) break;
+                cudaError_t e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e != cudaSuccess) s = cuda_fail(e, "autotune timing");
+                ms = std::min(ms, t);
             }
+            if (s != FS_OK) break;
             if (ms < best_t) {
                 best_t = ms;
                 bc.block_threads = t;
