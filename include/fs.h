@@ -186,6 +186,53 @@ fs_status fs_enumerate_async(int64_t n, const uint32_t* gens, int d, const fs_co
                              void* dev_buf, uint64_t cap, int elem_bytes, uint64_t* dev_count,
                              void* stream);
 
+/* --- resumable cursor and streamed enumerate ------------------------------ */
+
+/* A stream's next value depends only on its current state (Sec. 2), which is
+ * why the paper's enumeration has no memory limit on the result set (Table 1
+ * caption): it never needs the whole set at once.  A cursor gives the same
+ * property to the library's ordered output (the row order of fs_enumerate_ex
+ * for the same cfg): it plans the query and counts every slice once, then
+ * produces any window of rows on demand, so a result larger than device
+ * memory can be consumed piece by piece, and a consumer can stop and resume
+ * at any row.
+ *
+ * fs_cursor_create: plans and counts (synchronises `stream` once); the cursor
+ *   owns a small device allocation (the query's tables, slice states and
+ *   offsets; not the rows).  elem_bytes as fs_enumerate.  PAIR walk only
+ *   (FS_E_NOTIMPL for cfg->method PLAIN, TRIPLE or QUAD).
+ * fs_cursor_count: |Z| (host).  fs_cursor_tell: the next row to be produced.
+ * fs_cursor_slices: the number of slices the rows are cut into (host); a
+ *   window touches only the slices that hold its rows.
+ * fs_cursor_seek: continue from any row 0 <= row <= |Z| (FS_E_INVAL beyond).
+ * fs_cursor_next: enqueues on `stream` the rows [pos, pos + m) into dev_buf
+ *   (DEVICE, 16-byte aligned, room for cap rows of d elements), m = min(cap,
+ *   |Z| - pos), sets *rows = m (host, known at return) and advances pos by m;
+ *   m = 0 at the end.  Rows are written in stream order; calls on one cursor
+ *   share its device counters, so order them on one stream (or by events).
+ * fs_cursor_destroy: waits for the device and frees the cursor. */
+typedef struct fs_cursor fs_cursor;
+fs_status fs_cursor_create(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                           int elem_bytes, void* stream, fs_cursor** out);
+fs_status fs_cursor_count(const fs_cursor* c, uint64_t* total);
+fs_status fs_cursor_tell(const fs_cursor* c, uint64_t* row);
+fs_status fs_cursor_slices(const fs_cursor* c, uint64_t* slices);
+fs_status fs_cursor_seek(fs_cursor* c, uint64_t row);
+fs_status fs_cursor_next(fs_cursor* c, void* dev_buf, uint64_t cap, uint64_t* rows, void* stream);
+fs_status fs_cursor_destroy(fs_cursor* c);
+
+/* fs_enumerate into HOST memory: the same rows and return values as
+ * fs_enumerate_ex (FS_E_CAPACITY with the first cap rows written when |Z| >
+ * cap), streamed through two device staging buffers of up to 128 MB: the walk
+ * of one window overlaps the device-to-host copy of the previous one on a
+ * second stream.  host_buf (HOST, cap rows of d elements) should be pinned
+ * (cudaHostAlloc) for full bandwidth; pageable memory works but copies
+ * synchronously.  Synchronous: returns after every row is in host_buf.
+ * PAIR walk only, as the cursor. */
+fs_status fs_enumerate_host(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                            void* host_buf, uint64_t cap, int elem_bytes, uint64_t* out_count,
+                            void* stream);
+
 /* --- slice planner (Sec. 4) ---------------------------------------------- */
 
 /* The slices the walk uses.  A "leaf" is a prefix (a_1..a_{d-2}) of the walk

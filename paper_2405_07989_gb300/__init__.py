@@ -108,6 +108,16 @@ SIGNATURES = {
     "fs_count_async": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp, _vp]),
     "fs_enumerate_async": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp,
                                           ctypes.c_uint64, ctypes.c_int, _vp, _vp]),
+    "fs_cursor_create": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, ctypes.c_int,
+                                        _vp, ctypes.POINTER(ctypes.c_void_p)]),
+    "fs_cursor_count": (ctypes.c_int, [_vp, _u64p]),
+    "fs_cursor_tell": (ctypes.c_int, [_vp, _u64p]),
+    "fs_cursor_slices": (ctypes.c_int, [_vp, _u64p]),
+    "fs_cursor_seek": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "fs_cursor_next": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, _u64p, _vp]),
+    "fs_cursor_destroy": (ctypes.c_int, [_vp]),
+    "fs_enumerate_host": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp,
+                                         ctypes.c_uint64, ctypes.c_int, _u64p, _vp]),
     "fs_plan": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, ctypes.c_int64,
                                _i32p, _i32p, _u64p]),
     "fs_slice_counts": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
@@ -276,6 +286,81 @@ def fs_enumerate_async(n: int, gens, out, cap: int, dev_count, elem_bytes: int =
     g, d = _gens(gens)
     _check(lib().fs_enumerate_async(int(n), g, d, _cfgp_of(cfg), _ptr(out), int(cap),
                                     int(elem_bytes), _ptr(dev_count), _stream(stream)))
+
+
+class Cursor:
+    """fs_cursor_*: the ordered rows of Z(n, gens), produced window by window.
+    next(out) writes up to out's rows into the CUDA tensor `out` and returns
+    how many; count / tell / seek as the C functions."""
+
+    def __init__(self, n: int, gens, elem_bytes: int = 4, cfg: fs_config | None = None,
+                 stream=None):
+        g, d = _gens(gens)
+        self.d = d
+        h = ctypes.c_void_p(0)
+        _check(lib().fs_cursor_create(int(n), g, d, _cfgp_of(cfg), int(elem_bytes),
+                                      _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def count(self) -> int:
+        v = ctypes.c_uint64(0)
+        _check(lib().fs_cursor_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def tell(self) -> int:
+        v = ctypes.c_uint64(0)
+        _check(lib().fs_cursor_tell(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def slices(self) -> int:
+        v = ctypes.c_uint64(0)
+        _check(lib().fs_cursor_slices(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def seek(self, row: int) -> None:
+        _check(lib().fs_cursor_seek(self._h, int(row)))
+
+    def next(self, out, cap: int | None = None, stream=None) -> int:
+        if cap is None:
+            cap = out.numel() // max(self.d, 1)
+        m = ctypes.c_uint64(0)
+        _check(lib().fs_cursor_next(self._h, _ptr(out), int(cap), ctypes.byref(m),
+                                    _stream(stream)))
+        return int(m.value)
+
+    def close(self):
+        if self._h:
+            lib().fs_cursor_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fs_enumerate_host(n: int, gens, out, cap: int | None = None, elem_bytes: int = 4,
+                      cfg: fs_config | None = None, stream=None,
+                      allow_capacity: bool = False) -> int:
+    """Write Z(n, gens) into the HOST tensor `out` (pinned for full speed),
+    streamed through device staging buffers; returns |Z|."""
+    g, d = _gens(gens)
+    if cap is None:
+        cap = out.numel() // max(d, 1) if out is not None else 0
+    cnt = ctypes.c_uint64(0)
+    st = lib().fs_enumerate_host(int(n), g, d, _cfgp_of(cfg), _ptr(out), int(cap),
+                                 int(elem_bytes), ctypes.byref(cnt), _stream(stream))
+    if st == FS_E_CAPACITY and allow_capacity:
+        return int(cnt.value)
+    _check(st)
+    return int(cnt.value)
 
 
 def fs_plan(n: int, gens, slices: int, cfg: fs_config | None = None):

@@ -44,6 +44,12 @@ struct DevState {
     size_t size = 0;
     uint64_t* pinned = nullptr;
     int sms = 0;
+    // fs_enumerate_host: two device staging buffers, a copy stream, events
+    void* stage = nullptr;
+    size_t stage_size = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_comp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
 };
 
 std::mutex g_mu;
@@ -277,6 +283,10 @@ int method_of(const fs_config& c)
 
 // The query the trailing-k walk runs over: the first D-k levels as prefix
 // levels (k - 2 fewer than PAIR); the last k come from the trailing tables.
+// Enumerate counts its slices run by run from the trailing-three table (n + 1
+// uint64 entries) below this n, leaf by leaf above it.
+constexpr int32_t RUNS_MAX_N = 1 << 20;
+
 // Trailing levels the tables can take for q under `method` (0: none).
 // k = 3 needs D >= 4 (one prefix level left) and n < 2^27 (the length
 // sentinels stay in int32); k = 4 needs D >= 5 and n < 2^22, so that a table
@@ -397,6 +407,9 @@ Scratch scratch_at(void* base, const Layout& L)
     s.YD = (int32_t*)(b + L.YD);
     s.slice_cnt = (uint64_t*)(b + L.cnt);
     s.slice_off = (uint64_t*)(b + L.off);
+    s.s_lo = 0;
+    s.s_hi = ~0ull;
+    s.row_lo = 0;
     s.D = (uint64_t*)(b + L.D);
     s.starts = (int32_t*)(b + L.starts);
     return s;
@@ -431,6 +444,8 @@ struct Call {
     fs_config cfg;
     int method = FS_METHOD_PAIR;  // PLAIN, PAIR, or TRIPLE for the trailing-k tables
     int trail = 0;                // TRIPLE: k = 3 or 4 trailing levels in the tables
+    bool runs = false;            // PAIR enumerate: per-slice counts run by run from T3
+    Op op = OP_COUNT;
     DevState* ds = nullptr;
     Scratch sc;
     Layout L;
@@ -442,9 +457,10 @@ struct Call {
     const QueryConst& wq() const { return method == FS_METHOD_TRIPLE ? q3 : Q.q; }
 };
 
+// Host half of a call: query, method, launch geometry and scratch layout.
 // lengths_only: an OP_LEN call that wants no histogram (TRIPLE can serve it)
-fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_config* cfg, Op op,
-                  int eb, void* stream, size_t extra_bytes = 0, bool lengths_only = false)
+fs_status prepare_host(Call& c, int64_t n, const uint32_t* gens, int d, const fs_config* cfg, Op op,
+                       int eb, void* stream, size_t extra_bytes = 0, bool lengths_only = false)
 {
     c.cfg = cfg_or_default(cfg);
     c.st = (cudaStream_t)stream;
@@ -473,6 +489,9 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
     }
     const bool triple = c.method == FS_METHOD_TRIPLE;
     if (triple) c.q3 = reduce_trailing(c.Q.q, c.trail);
+    // enumerate's first walk (per-slice counts) goes run by run over the
+    // trailing-three table when the table is small
+    c.runs = op == OP_ENUM && c.method == FS_METHOD_PAIR && c.Q.q.n < RUNS_MAX_N;
     const QueryConst& qw = c.wq();
     s = get_dev(&c.ds);
     if (s != FS_OK) return s;
@@ -481,12 +500,21 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
     s = geometry(qw, c.cfg, op == OP_ENUM && c.method == FS_METHOD_PAIR ? OP_ENUM : op, c.method,
                  eb, c.ds->sms, c.lc);
     if (s != FS_OK) return s;
-    c.L = make_layout(qw, c.lc.S, extra_bytes, triple);
-    s = ensure_arena(c.ds, c.L.total);
-    if (s != FS_OK) return s;
-    c.sc = scratch_at(c.ds->arena, c.L);
-    if (triple) {
-        char* b = (char*)c.ds->arena;
+    c.L = make_layout(qw, c.lc.S, extra_bytes, triple || c.runs);
+    c.op = op;
+    return FS_OK;
+}
+
+// Device half: the scratch at `base` (c.L.total bytes), counter reset,
+// precompute and planner launches.
+fs_status prepare_device(Call& c, void* base)
+{
+    const bool triple = c.method == FS_METHOD_TRIPLE;
+    const QueryConst& qw = c.wq();
+    const Op op = c.op;
+    c.sc = scratch_at(base, c.L);
+    if (triple || c.runs) {
+        char* b = (char*)base;
         c.T3 = (uint64_t*)(b + c.L.T3);
         c.MN3 = (int32_t*)(b + c.L.MN3);
         c.MX3 = (int32_t*)(b + c.L.MX3);
@@ -495,10 +523,14 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     {
         ProfScope ps("precompute", c.st,
-                     ((qw.tab_e || qw.tab_xy) ? 1 : 0) + (qw.nw > 0 ? 1 : 0) + (triple ? 1 : 0));
+                     ((qw.tab_e || qw.tab_xy) ? 1 : 0) + (qw.nw > 0 ? 1 : 0) +
+                         ((triple || c.runs) ? 1 : 0));
         e = launch_precompute(qw, c.sc, c.st);
+        const bool lens = op == OP_LEN;  // the length tables only where they are read
         if (e == cudaSuccess && triple)
-            e = launch_trailing_tables(c.Q.q, c.trail, c.T3, c.MN3, c.MX3, c.st);
+            e = launch_trailing_tables(c.Q.q, c.trail, c.T3, lens ? c.MN3 : nullptr,
+                                       lens ? c.MX3 : nullptr, c.st);
+        if (e == cudaSuccess && c.runs) e = launch_trailing_tables(c.Q.q, 3, c.T3, nullptr, nullptr, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
     {
@@ -507,6 +539,17 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
     }
     if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     return FS_OK;
+}
+
+// Both halves, with the scratch in the device's shared arena.
+fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_config* cfg, Op op,
+                  int eb, void* stream, size_t extra_bytes = 0, bool lengths_only = false)
+{
+    fs_status s = prepare_host(c, n, gens, d, cfg, op, eb, stream, extra_bytes, lengths_only);
+    if (s != FS_OK) return s;
+    s = ensure_arena(c.ds, c.L.total);
+    if (s != FS_OK) return s;
+    return prepare_device(c, c.ds->arena);
 }
 
 fs_status read_ctr(Call& c)
@@ -543,20 +586,77 @@ fs_status do_count(Call& c, uint64_t* dev_count)
     return FS_OK;
 }
 
-fs_status do_enum(Call& c, void* dev_buf, uint64_t cap, int eb, uint64_t* dev_count)
+// Enumerate, first walk and scan: every slice's count, then its row offset.
+fs_status enum_count_slices(Call& c, uint64_t* dev_count)
 {
-    // first walk: per-slice counts; scan: per-slice offsets; second walk: rows
-    cudaError_t e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, eb, c.st);
+    cudaError_t e;
+    if (c.runs) {
+        ProfScope ps("pair_slice_runs", c.st, 1);
+        const uint64_t blocks = std::min<uint64_t>((c.lc.S + 7) / 8, 4096);
+        e = launch_pair_slice_runs(c.Q.q, c.sc, c.T3, (int)blocks, c.st);
+    } else {
+        e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "enumerate count launch");
     {
         ProfScope ps("scan_slices", c.st, 1);
         e = launch_scan_slices(c.sc, dev_count, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
-    if (cap > 0) {
-        e = launch_walk(c.Q.q, c.sc, OP_ENUM, c.method, c.lc, CTR_QUEUE2, nullptr, dev_buf, cap, eb, c.st);
-        if (e != cudaSuccess) return cuda_fail(e, "enumerate write launch");
-    }
+    return FS_OK;
+}
+
+// Enumerate, second walk: the rows of the slices in sc's window into dev_buf
+// (cap rows from global row sc.row_lo on).
+fs_status enum_write(Call& c, const Scratch& sc, void* dev_buf, uint64_t cap, int eb, cudaStream_t st)
+{
+    if (cap == 0) return FS_OK;
+    cudaError_t e = launch_walk(c.Q.q, sc, OP_ENUM, c.method, c.lc, CTR_QUEUE2, nullptr, dev_buf, cap, eb, st);
+    if (e != cudaSuccess) return cuda_fail(e, "enumerate write launch");
+    return FS_OK;
+}
+
+fs_status do_enum(Call& c, void* dev_buf, uint64_t cap, int eb, uint64_t* dev_count)
+{
+    fs_status s = enum_count_slices(c, dev_count);
+    if (s == FS_OK) s = enum_write(c, c.sc, dev_buf, cap, eb, c.st);
+    return s;
+}
+
+// The slices [s0, s1) that hold rows [pos, pos + rows) of the ordered
+// output, from the host copy of the slice offsets (off[0..S]).
+void window_slices(const std::vector<uint64_t>& off, uint64_t S, uint64_t pos, uint64_t rows,
+                   uint64_t* s0, uint64_t* s1)
+{
+    const auto b = off.begin(), e = off.begin() + (ptrdiff_t)S + 1;
+    *s0 = (uint64_t)(std::upper_bound(b, e, pos) - b) - 1;
+    *s1 = (uint64_t)(std::lower_bound(b, e, pos + rows) - b);
+}
+
+// Rows [pos, pos + rows) of the ordered output into dev_buf: the write walk
+// over the slices that hold them, rows outside the window dropped.
+fs_status enum_window(Call& c, const std::vector<uint64_t>& off, uint64_t S, uint64_t pos,
+                      uint64_t rows, void* dev_buf, int eb, cudaStream_t st)
+{
+    Scratch sc = c.sc;
+    window_slices(off, S, pos, rows, &sc.s_lo, &sc.s_hi);
+    sc.row_lo = pos;
+    cudaError_t e = cudaMemsetAsync(&c.sc.ctr[CTR_QUEUE2], 0, 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    return enum_write(c, sc, dev_buf, rows, eb, st);
+}
+
+// The slice offsets to the host after enum_count_slices (synchronises c.st).
+fs_status fetch_offsets(Call& c, uint64_t* S, uint64_t* total, std::vector<uint64_t>& off)
+{
+    fs_status s = read_ctr(c);
+    if (s != FS_OK) return s;
+    *S = c.ds->pinned[CTR_SEFF];
+    *total = c.ds->pinned[CTR_TOTAL];
+    off.resize(*S + 1);
+    cudaError_t e = cudaMemcpyAsync(off.data(), c.sc.slice_off, (*S + 1) * 8, cudaMemcpyDeviceToHost, c.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice offsets to host");
     return FS_OK;
 }
 
@@ -754,6 +854,218 @@ fs_status fs_enumerate_async(int64_t n, const uint32_t* gens, int d, const fs_co
     fs_status s = prepare(c, n, gens, d, cfg, OP_ENUM, elem_bytes, stream);
     if (s == FS_OK) s = do_enum(c, dev_buf, cap, elem_bytes, dev_count);
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// resumable cursor and streamed enumerate
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct fs_cursor {
+    Call c;
+    void* mem = nullptr;  // the cursor's own scratch (c.L.total bytes)
+    int eb = 4;
+    uint64_t S = 0, total = 0, pos = 0;
+    std::vector<uint64_t> off;  // row offset of every slice, S + 1 entries
+};
+
+namespace {
+
+fs_status stage_ready(DevState* ds, size_t bytes)
+{
+    if (!ds->copy_st) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ds->copy_st, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+            e = cudaEventCreateWithFlags(&ds->ev_comp[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ds->ev_copy[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+    }
+    if (ds->stage_size >= bytes) return FS_OK;
+    if (ds->stage) {
+        cudaDeviceSynchronize();
+        cudaFree(ds->stage);
+        ds->stage = nullptr;
+        ds->stage_size = 0;
+    }
+    cudaError_t e = cudaMalloc(&ds->stage, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ds->stage = nullptr;
+        return fail(FS_E_NOMEM, "staging cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    ds->stage_size = bytes;
+    return FS_OK;
+}
+
+// Staging chunk of fs_enumerate_host: large enough that each window's launch
+// is small beside its copy, small enough to overlap the next window's walk.
+constexpr size_t STAGE_CHUNK_BYTES = 128u << 20;
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs_cursor_create(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                           int elem_bytes, void* stream, fs_cursor** out)
+{
+    if (!out) return fail(FS_E_INVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    {
+        Query Q;
+        fs_status s = build_query(n, gens, d, cfg_or_default(cfg), Q);
+        if (s != FS_OK) return s;
+        s = check_enum_args(Q, nullptr, 0, elem_bytes);
+        if (s != FS_OK) return s;
+    }
+    fs_cursor* k = new fs_cursor;
+    Call& c = k->c;
+    fs_status s = prepare_host(c, n, gens, d, cfg, OP_ENUM, elem_bytes, stream);
+    if (s == FS_OK && c.method != FS_METHOD_PAIR)
+        s = fail(FS_E_NOTIMPL, "a cursor walks the PAIR method (method %d asked)", c.cfg.method);
+    if (s == FS_OK) {
+        cudaError_t e = cudaMalloc(&k->mem, c.L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            k->mem = nullptr;
+            s = fail(FS_E_NOMEM, "cursor cudaMalloc(%zu): %s", c.L.total, cudaGetErrorString(e));
+        }
+    }
+    if (s == FS_OK) s = prepare_device(c, k->mem);
+    if (s == FS_OK) s = enum_count_slices(c, nullptr);
+    if (s == FS_OK) s = fetch_offsets(c, &k->S, &k->total, k->off);
+    if (s != FS_OK) {
+        if (k->mem) {
+            cudaDeviceSynchronize();
+            cudaFree(k->mem);
+        }
+        delete k;
+        return s;
+    }
+    k->eb = elem_bytes;
+    *out = k;
+    return FS_OK;
+}
+
+fs_status fs_cursor_count(const fs_cursor* k, uint64_t* total)
+{
+    if (!k || !total) return fail(FS_E_INVAL, "cursor / total is NULL");
+    *total = k->total;
+    return FS_OK;
+}
+
+fs_status fs_cursor_tell(const fs_cursor* k, uint64_t* row)
+{
+    if (!k || !row) return fail(FS_E_INVAL, "cursor / row is NULL");
+    *row = k->pos;
+    return FS_OK;
+}
+
+fs_status fs_cursor_slices(const fs_cursor* k, uint64_t* slices)
+{
+    if (!k || !slices) return fail(FS_E_INVAL, "cursor / slices is NULL");
+    *slices = k->S;
+    return FS_OK;
+}
+
+fs_status fs_cursor_seek(fs_cursor* k, uint64_t row)
+{
+    if (!k) return fail(FS_E_INVAL, "cursor is NULL");
+    if (row > k->total)
+        return fail(FS_E_INVAL, "seek to row %llu of %llu", (unsigned long long)row,
+                    (unsigned long long)k->total);
+    k->pos = row;
+    return FS_OK;
+}
+
+fs_status fs_cursor_next(fs_cursor* k, void* dev_buf, uint64_t cap, uint64_t* rows, void* stream)
+{
+    if (!k || !rows) return fail(FS_E_INVAL, "cursor / rows is NULL");
+    if (cap > 0 && !dev_buf) return fail(FS_E_INVAL, "dev_buf is NULL");
+    if (((uintptr_t)dev_buf & 15) != 0) return fail(FS_E_INVAL, "dev_buf is not 16-byte aligned");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const uint64_t left = k->total - k->pos;
+    const uint64_t m = cap < left ? cap : left;
+    *rows = m;
+    if (m == 0) return FS_OK;
+    fs_status s = enum_window(k->c, k->off, k->S, k->pos, m, dev_buf, k->eb, (cudaStream_t)stream);
+    if (s == FS_OK) k->pos += m;
+    return s;
+}
+
+fs_status fs_cursor_destroy(fs_cursor* k)
+{
+    if (!k) return FS_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (k->mem) cudaFree(k->mem);
+    delete k;
+    if (e != cudaSuccess) return cuda_fail(e, "cursor free");
+    return FS_OK;
+}
+
+fs_status fs_enumerate_host(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                            void* host_buf, uint64_t cap, int elem_bytes, uint64_t* out_count,
+                            void* stream)
+{
+    if (!out_count) return fail(FS_E_INVAL, "out_count is NULL");
+    if (cap > 0 && !host_buf) return fail(FS_E_INVAL, "host_buf is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    {
+        Query Q;
+        fs_status s = build_query(n, gens, d, cfg_or_default(cfg), Q);
+        if (s != FS_OK) return s;
+        s = check_enum_args(Q, nullptr, 0, elem_bytes);
+        if (s != FS_OK) return s;
+        if (cap > (~0ull) / (uint64_t)Q.q.d / 4) return fail(FS_E_INVAL, "cap too large");
+    }
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_ENUM, elem_bytes, stream);
+    if (s == FS_OK && c.method != FS_METHOD_PAIR)
+        s = fail(FS_E_NOTIMPL, "fs_enumerate_host walks the PAIR method (method %d asked)", c.cfg.method);
+    if (s == FS_OK) s = enum_count_slices(c, nullptr);
+    uint64_t S = 0, total = 0;
+    std::vector<uint64_t> off;
+    if (s == FS_OK) s = fetch_offsets(c, &S, &total, off);
+    if (s != FS_OK) return s;
+    *out_count = total;
+    const uint64_t want = cap < total ? cap : total;
+    const size_t row_bytes = (size_t)c.Q.q.d * (size_t)elem_bytes;
+    if (want > 0) {
+        uint64_t chunk = STAGE_CHUNK_BYTES / row_bytes;
+        if (chunk > want) chunk = want;
+        if (chunk < 1) chunk = 1;
+        const size_t half = al((size_t)chunk * row_bytes);
+        DevState* ds = c.ds;
+        s = stage_ready(ds, 2 * half);
+        if (s != FS_OK) return s;
+        cudaError_t e = cudaSuccess;
+        uint64_t k = 0;
+        for (uint64_t pos = 0; pos < want && s == FS_OK && e == cudaSuccess; k++) {
+            const uint64_t rows = chunk < want - pos ? chunk : want - pos;
+            void* buf = (char*)ds->stage + (k & 1) * half;
+            if (k >= 2) e = cudaStreamWaitEvent(c.st, ds->ev_copy[k & 1], 0);  // buffer drained
+            if (e == cudaSuccess) s = enum_window(c, off, S, pos, rows, buf, elem_bytes, c.st);
+            if (s != FS_OK) break;
+            e = cudaEventRecord(ds->ev_comp[k & 1], c.st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ds->copy_st, ds->ev_comp[k & 1], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char*)host_buf + pos * row_bytes, buf, rows * row_bytes,
+                                    cudaMemcpyDeviceToHost, ds->copy_st);
+            if (e == cudaSuccess) e = cudaEventRecord(ds->ev_copy[k & 1], ds->copy_st);
+            pos += rows;
+        }
+        const cudaError_t e2 = cudaStreamSynchronize(ds->copy_st);
+        if (s != FS_OK) return s;
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return cuda_fail(e, "streamed enumerate");
+        s = read_ctr(c);  // the write walks' fault flag
+        if (s != FS_OK) return s;
+    }
+    if (total > cap)
+        return fail(FS_E_CAPACITY, "%llu factorizations, capacity %llu", (unsigned long long)total,
+                    (unsigned long long)cap);
+    return FS_OK;
 }
 
 fs_status fs_plan(int64_t n, const uint32_t* gens, int d, const fs_config* cfg, int64_t slices,
@@ -1289,6 +1601,7 @@ extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, ui
     char* base = (char*)g_noalloc_addr[dev];
     Scratch sc;
     memset(&sc, 0, sizeof sc);
+    sc.s_hi = ~0ull;
     sc.ctr = (uint64_t*)base;
     sc.W = (uint64_t*)(base + off_W);
     sc.E = (int8_t*)(base + off_E);

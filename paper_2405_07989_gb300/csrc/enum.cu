@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(256, 3) k_pair_enum(const __grid_constant__ Qu
     C cons;
     cons.sg.out = out;
     cons.sg.cap_elems = cap_rows * (uint64_t)q.d;
+    cons.sg.lo_elems = sc.row_lo * (uint64_t)q.d;
     cons.sg.wbase = wp;
     cons.sg.buf = 0;
     cons.sg.d = q.d;

@@ -29,15 +29,19 @@ FS_D void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memo
 
 // Per-warp staging of consecutive output rows in shared memory, drained by
 // the bulk-copy engine.  The staged rows are the global rows
-// [row_base, row_base + nst); element e of the staged block sits at index
-// phase + e of the current buffer, with phase = (row_base d) mod VEC so that
-// 16-byte boundaries line up with the output's.
+// [row_base, row_base + nst); global element g (= row * d + column) goes to
+// out[g - lo_elems] when 0 <= g - lo_elems < cap_elems and is dropped
+// otherwise (the window of a cursor; lo_elems = 0 for a whole enumerate).
+// Staged element e sits at index phase + e of the current buffer, with
+// phase = (row_base d - lo_elems) mod VEC so that 16-byte boundaries line up
+// with the output's.
 template <typename ELEM>
 struct Stager {
     static constexpr int VEC = 16 / (int)sizeof(ELEM);
     static constexpr int STG = ENUM_STG_BYTES / (int)sizeof(ELEM);
     ELEM* out;
     uint64_t cap_elems;
+    uint64_t lo_elems;
     unsigned char* wbase;  // this warp's two buffers
     uint64_t row_base;
     int32_t buf, nst, phase, d;
@@ -45,37 +49,43 @@ struct Stager {
     FS_D ELEM* stg(int k) const { return (ELEM*)(wbase + k * ENUM_STG_BYTES); }
     FS_D ELEM* cursor() const { return stg(buf) + phase + nst * d; }
     FS_D bool fits(int rows) const { return phase + (nst + rows) * d <= STG; }
+    // window position of the first staged element (negative: before the window)
+    FS_D int64_t wpos() const { return (int64_t)(row_base * (uint64_t)d) - (int64_t)lo_elems; }
 
     FS_D void begin(uint64_t row0)
     {
         row_base = row0;
         nst = 0;
-        phase = (int32_t)((row_base * (uint64_t)d) % VEC);
+        phase = (int32_t)(((wpos() % VEC) + VEC) % VEC);
     }
 
-    // Write the staged rows out (rows past cap are dropped) and switch buffers.
+    // Write the staged rows that fall in the window and switch buffers.
     FS_D void flush()
     {
         const int lane = threadIdx.x & 31;
         __syncwarp();  // every lane's staged rows are in place
         if (nst > 0) {
             const ELEM* sb = stg(buf);
-            const uint64_t g0 = row_base * (uint64_t)d;
-            const uint64_t N = (uint64_t)nst * (uint64_t)d;
-            const uint64_t gend = (g0 + N < cap_elems) ? g0 + N : cap_elems;
-            if (g0 < gend) {
-                const uint32_t span = (uint32_t)(gend - g0);
+            const int64_t e0 = wpos();
+            const int64_t N = (int64_t)nst * d;
+            const int64_t lo = e0 > 0 ? e0 : 0;
+            const int64_t hi = (e0 + N < (int64_t)cap_elems) ? e0 + N : (int64_t)cap_elems;
+            if (lo < hi) {
+                // staged index of window element e: phase + (e - e0)
+                const int32_t sb0 = phase + (int32_t)(lo - e0);
+                const uint64_t g0 = (uint64_t)lo;
+                const uint32_t span = (uint32_t)(hi - lo);
                 uint32_t head = (uint32_t)((VEC - g0 % VEC) % VEC);
                 if (head > span) head = span;
                 const uint32_t nv = (span - head) / VEC;
                 const uint32_t tail0 = head + nv * VEC;
-                if ((uint32_t)lane < head) out[g0 + lane] = sb[phase + lane];
-                for (uint32_t i = tail0 + lane; i < span; i += 32) out[g0 + i] = sb[phase + i];
+                if ((uint32_t)lane < head) out[g0 + lane] = sb[sb0 + lane];
+                for (uint32_t i = tail0 + lane; i < span; i += 32) out[g0 + i] = sb[sb0 + i];
                 if (nv > 0) {
                     fence_proxy_async_smem();  // staging writes -> visible to the bulk copy
                     __syncwarp();
                     if (lane == 0) {
-                        bulk_store(out + g0 + head, sb + phase + head, nv * 16u);
+                        bulk_store(out + g0 + head, sb + sb0 + head, nv * 16u);
                         bulk_commit();
                     }
                 }
@@ -87,7 +97,7 @@ struct Stager {
         }
         row_base += (uint64_t)nst;
         nst = 0;
-        phase = (int32_t)((row_base * (uint64_t)d) % VEC);
+        phase = (int32_t)(((wpos() % VEC) + VEC) % VEC);
     }
 
     FS_D void finish()

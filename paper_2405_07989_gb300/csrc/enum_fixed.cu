@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256, 3) k_pair_enum_fix(const __grid_constant_
     C cons;
     cons.sg.out = out;
     cons.sg.cap_elems = cap_rows * (uint64_t)D;
+    cons.sg.lo_elems = sc.row_lo * (uint64_t)D;
     cons.sg.wbase = wp;
     cons.sg.buf = 0;
     cons.sg.d = D;

@@ -119,6 +119,10 @@ struct Scratch {
     uint64_t* slice_off;  // S + 1
     uint64_t* D;          // dbins (global difference array)
     int32_t* starts;      // S * FS_MAX_D slice start states (planner output)
+    // the window a walk covers: slices [s_lo, min(S, s_hi)); an enumerate
+    // writes global row g to row g - row_lo of its buffer (rows outside
+    // [row_lo, row_lo + cap) are dropped)
+    uint64_t s_lo, s_hi, row_lo;
 };
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,8 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
 // pair.cu: the TRIPLE walk over the reduced query q3 (OP_COUNT, OP_SLICES,
 // OP_LEN = count + min / max length)
 cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
+cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
+                                   int blocks, cudaStream_t st);
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
                           int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
                           cudaStream_t st);

@@ -340,6 +340,39 @@ __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ Que
     }
 }
 
+// Per-slice counts of PAIR slices from the trailing-three table, run by run
+// (slice_count_runs): the first walk of fs_enumerate when the table is cheap.
+// Slices are few thousand leaves each and take a handful of warp steps, so a
+// plain grid-stride over slices balances them.
+__global__ void __launch_bounds__(256) k_pair_slice_runs(const __grid_constant__ QueryConst q,
+                                                         Scratch sc, const uint64_t* T3)
+{
+    __shared__ SmemQ sq;
+    load_smemq(q, sq);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
+    const uint64_t S = sc.ctr[CTR_SEFF];
+    const SliceSplit split(sc.ctr[CTR_L], S);
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    bool fault = false;
+    for (uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+        const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
+        uint64_t c = 0;
+        if (k1 > k0) c = slice_count_runs(q, sq.h, sq.dvh, sc.starts, s, k1 - k0, lane, hk, T3, &fault);
+        c = warp_sum_u64(c);
+        if (lane == 0) sc.slice_cnt[s] = c;
+    }
+    if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
+}
+
+cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
+                                   int blocks, cudaStream_t st)
+{
+    k_pair_slice_runs<<<blocks, 256, 0, st>>>(q, sc, T3);
+    return cudaGetLastError();
+}
+
 cudaError_t triple_occupancy(int threads, int* nb)
 {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_triple_walk<1, false>, threads, 0);

@@ -34,21 +34,17 @@ __global__ void __launch_bounds__(1024) k_weights(const __grid_constant__ QueryC
     }
 }
 
+// Leaf-count tables up to this size are staged in shared memory by the planner.
+constexpr size_t PLAN_SMEM_MAX = 160 * 1024;
+
 // The slice planner (Sec. 4, the role of Algorithm 4.1): S_req slices, or with
 // auto_s as many as keep about min_leaves leaves per slice (at most S_req);
 // writes the count and every slice's start (its first leaf, found by
-// warp_unrank on the exact leaf counts).  One warp per slice.
-__global__ void __launch_bounds__(256) k_plan(const __grid_constant__ QueryConst q, Scratch sc,
-                                              uint64_t S_req, int auto_s, uint64_t min_leaves)
+// warp_unrank on the exact leaf counts W).  One warp per slice, grid-stride.
+FS_D void plan_slices(const QueryConst& q, const Scratch& sc, const uint64_t* W, const int32_t* hs,
+                      const Div32* dvh, uint64_t S_req, int auto_s, uint64_t min_leaves)
 {
-    __shared__ int32_t hs[FS_MAX_D];
-    __shared__ Div32 dvh[FS_MAX_D];
-    if (threadIdx.x < FS_MAX_D) {
-        hs[threadIdx.x] = q.h[threadIdx.x];
-        dvh[threadIdx.x] = q.dv_h[threadIdx.x];
-    }
-    __syncthreads();
-    const uint64_t L = total_leaves(q, sc.W);
+    const uint64_t L = total_leaves(q, W);
     uint64_t S = S_req;
     if (auto_s) {
         uint64_t want = (L + min_leaves - 1) / min_leaves;
@@ -71,44 +67,123 @@ __global__ void __launch_bounds__(256) k_plan(const __grid_constant__ QueryConst
             continue;
         }
         RunPrefix rp;
-        const int32_t b = warp_unrank(q, hs, dvh, sc.W, k0, lane, rp);
+        const int32_t b = warp_unrank(q, hs, dvh, W, k0, lane, rp);
         if (lane < q.P - 1) st[lane] = rp.a;
         if (lane == 0) st[START_W - 1] = b;
     }
 }
 
+__global__ void __launch_bounds__(256) k_plan(const __grid_constant__ QueryConst q, Scratch sc,
+                                              uint64_t S_req, int auto_s, uint64_t min_leaves)
+{
+    __shared__ int32_t hs[FS_MAX_D];
+    __shared__ Div32 dvh[FS_MAX_D];
+    if (threadIdx.x < FS_MAX_D) {
+        hs[threadIdx.x] = q.h[threadIdx.x];
+        dvh[threadIdx.x] = q.dv_h[threadIdx.x];
+    }
+    __syncthreads();
+    plan_slices(q, sc, sc.W, hs, dvh, S_req, auto_s, min_leaves);
+}
+
+// The same with the leaf-count tables staged in shared memory (when they
+// fit): one block per SM copies W once; its warps' probes then hit shared
+// memory instead of L2.
+__global__ void __launch_bounds__(1024) k_plan_smem(const __grid_constant__ QueryConst q, Scratch sc,
+                                                    uint64_t S_req, int auto_s, uint64_t min_leaves)
+{
+    __shared__ int32_t hs[FS_MAX_D];
+    __shared__ Div32 dvh[FS_MAX_D];
+    extern __shared__ __align__(16) unsigned char dyn[];
+    uint64_t* Ws = (uint64_t*)dyn;
+    if (threadIdx.x < FS_MAX_D) {
+        hs[threadIdx.x] = q.h[threadIdx.x];
+        dvh[threadIdx.x] = q.dv_h[threadIdx.x];
+    }
+    const uint32_t words = (uint32_t)q.nw * (uint32_t)(q.n + 1);
+    const ulonglong2* src = (const ulonglong2*)sc.W;  // 256-byte aligned section
+    ulonglong2* dst = (ulonglong2*)Ws;
+    for (uint32_t i = threadIdx.x; i < words / 2; i += blockDim.x) dst[i] = src[i];
+    if ((words & 1) && threadIdx.x == 0) Ws[words - 1] = sc.W[words - 1];
+    __syncthreads();
+    plan_slices(q, sc, Ws, hs, dvh, S_req, auto_s, min_leaves);
+}
+
 // off[s] = sum_{j < s} cnt[j] for s = 0..S (S = the planner's slice count),
-// total -> ctr[CTR_TOTAL] and (optionally) *dev_count.  One block; each thread
-// sums a contiguous run of slices, then a block scan of the runs.
+// total -> ctr[CTR_TOTAL] and (optionally) *dev_count.  One block, tiles of
+// 8 x blockDim slices: each thread loads 8 consecutive counts with four 16-byte
+// vector loads (all of a tile's loads in flight at once), scans them in
+// registers, and a warp-shuffle block scan of the thread totals places them.
 __global__ void __launch_bounds__(1024) k_scan_slices(const uint64_t* cnt, uint64_t* off,
                                                       uint64_t* ctr, uint64_t* dev_count)
 {
-    __shared__ uint64_t part[1024];
+    __shared__ uint64_t wsum[32];
     const uint64_t S = ctr[CTR_SEFF];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const uint64_t per = (S + T - 1) / T;
-    const uint64_t b = (uint64_t)tid * per;
-    const uint64_t e = b + per < S ? b + per : S;
-    uint64_t s = 0;
-#pragma unroll 8
-    for (uint64_t i = b; i < e; i++) s += cnt[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int o = 1; o < T; o <<= 1) {
-        uint64_t v = tid >= o ? part[tid - o] : 0;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nwarp = blockDim.x >> 5;
+    const uint64_t tile = 8ull * blockDim.x;
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < S; base += tile) {
+        const uint64_t i0 = base + 8ull * (uint64_t)tid;
+        uint64_t v[8];
+        if (i0 + 8 <= S) {
+            const ulonglong2* p = (const ulonglong2*)(cnt + i0);  // 64-byte aligned
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const ulonglong2 x = p[k];
+                v[2 * k] = x.x;
+                v[2 * k + 1] = x.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = i0 + k < S ? cnt[i0 + k] : 0;
+        }
+        uint64_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) sum += v[k];
+        uint64_t x = sum;  // inclusive scan of the thread totals within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[tid] += v;
+        if (w == 0) {
+            uint64_t y = lane < nwarp ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(FULL, y, o);
+                if (lane >= o) y += t;
+            }
+            if (lane < nwarp) wsum[lane] = y;
+        }
         __syncthreads();
+        uint64_t run = carry + (w > 0 ? wsum[w - 1] : 0) + x - sum;
+        if (i0 + 8 <= S) {
+            uint64_t o[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                o[k] = run;
+                run += v[k];
+            }
+            ulonglong2* q = (ulonglong2*)(off + i0);
+#pragma unroll
+            for (int k = 0; k < 4; k++) q[k] = make_ulonglong2(o[2 * k], o[2 * k + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                if (i0 + k < S) {
+                    off[i0 + k] = run;
+                    run += v[k];
+                }
+        }
+        carry += wsum[nwarp - 1];
+        __syncthreads();  // wsum is rewritten by the next tile
     }
-    uint64_t run = tid > 0 ? part[tid - 1] : 0;
-    for (uint64_t i = b; i < e; i++) {
-        off[i] = run;
-        run += cnt[i];
-    }
-    if (tid == T - 1) {
-        off[S] = part[T - 1];
-        ctr[CTR_TOTAL] = part[T - 1];
-        if (dev_count) *dev_count = part[T - 1];
+    if (tid == 0) {
+        off[S] = carry;
+        ctr[CTR_TOTAL] = carry;
+        if (dev_count) *dev_count = carry;
     }
 }
 
@@ -179,6 +254,20 @@ cudaError_t launch_scan_slices(const Scratch& sc, uint64_t* dev_count, cudaStrea
 cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
                         uint64_t min_leaves, cudaStream_t st)
 {
+    const size_t wbytes = (size_t)q.nw * (size_t)(q.n + 1) * 8;
+    if (wbytes > 0 && wbytes <= PLAN_SMEM_MAX && S_req >= 1024) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess && wbytes > 48 * 1024)
+            e = cudaFuncSetAttribute(k_plan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wbytes);
+        if (e != cudaSuccess) return e;
+        const uint64_t need = (S_req + 31) / 32;  // blocks of 32 warps
+        const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
+        k_plan_smem<<<blocks, 1024, wbytes, st>>>(q, sc, S_req, auto_s, min_leaves);
+        return cudaGetLastError();
+    }
     uint64_t blocks = (S_req + 7) / 8;  // one warp per slice
     if (blocks > 16384) blocks = 16384;
     if (blocks < 1) blocks = 1;

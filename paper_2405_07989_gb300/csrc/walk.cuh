@@ -387,6 +387,74 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
 }
 
 // ---------------------------------------------------------------------------
+// The same slice counted run by run: T3[p] (the trailing-three table of q:
+// the factorizations of p over levels P-1, P, P+1) is the count of all leaves
+// of a run from residual p downwards, so a run segment a_{P-1} = b .. b+m-1
+// with run residual R holds T3[R - b h] - T3[R - (b+m) h] factorizations
+// (the second term 0 when the segment reaches the run's end).  Lane j takes
+// sibling run j; the warp advances 32 runs per step instead of 32 leaves.
+// Returns this lane's part of the slice count (the caller sums the warp);
+// *fault is set if the slice claims leaves past the last one.
+// ---------------------------------------------------------------------------
+FS_D uint64_t slice_count_runs(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                               const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
+                               int32_t hk, const uint64_t* T3, bool* fault)
+{
+    RunPrefix rp;
+    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
+    const int np = q.P - 1;
+    const int32_t hin = hs[np];
+    uint64_t rem = nleaves;
+    uint64_t acc = 0;
+    for (;;) {
+        int32_t Rc = q.n, ac = 0;
+        uint32_t hsib = 0, nsib = 1;
+        if (np > 0) {
+            Rc = __shfl_sync(FULL, rp.r, np - 1);
+            ac = __shfl_sync(FULL, rp.a, np - 1);
+            hsib = (uint32_t)hs[np - 1];
+            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            if (nsib > 32) nsib = 32;
+        }
+        const bool act = (uint32_t)lane < nsib;
+        const int32_t R = (int32_t)((uint32_t)Rc - (uint32_t)lane * hsib);
+        const int32_t bj = lane == 0 ? b : 0;
+        // leaves this run still has (from bj on), and how many of them the slice takes
+        const uint64_t len = act ? (uint64_t)(div32((uint32_t)R, q.dv_in) + 1 - (uint32_t)bj) : 0;
+        uint64_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint64_t excl = incl - len;
+        const uint64_t m = excl >= rem ? 0 : (rem - excl < len ? rem - excl : len);
+        if (m > 0) {
+            const int32_t r0 = R - bj * hin;
+            const int32_t r1 = r0 - (int32_t)m * hin;
+            acc += __ldg(&T3[r0]) - (r1 >= 0 ? __ldg(&T3[r1]) : 0ull);
+        }
+        const uint64_t tot = __shfl_sync(FULL, incl, 31);
+        if (tot >= rem) return acc;
+        rem -= tot;
+        b = 0;
+        if (np == 0) {
+            *fault = true;
+            return acc;
+        }
+        if (lane == np - 1) {
+            rp.a = ac + (int32_t)nsib - 1;
+            rp.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
+            rp.l = 0;
+        }
+        if (!warp_next_run(q, lane, hk, rp)) {
+            *fault = true;
+            return acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Per-block copies of the dynamically indexed per-level constants, the slice
 // queue loop, and the device error flag.
 // ---------------------------------------------------------------------------
@@ -417,14 +485,15 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
 {
     const int lane = threadIdx.x & 31;
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
-    const uint64_t S = sc.ctr[CTR_SEFF];
-    const SliceSplit split(sc.ctr[CTR_L], S);
+    const uint64_t S_all = sc.ctr[CTR_SEFF];
+    const SliceSplit split(sc.ctr[CTR_L], S_all);
+    const uint64_t S = sc.s_hi < S_all ? sc.s_hi : S_all;  // the window's slices
     const uint64_t W = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
-    unsigned long long s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned long long s = sc.s_lo + (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     while (s < S) {
         unsigned long long nxt = 0;
-        if (lane == 0) nxt = atomicAdd(qc, 1ull) + W;
+        if (lane == 0) nxt = sc.s_lo + atomicAdd(qc, 1ull) + W;
         const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
         cons.slice_begin(q, s);
         bool stop = false;
@@ -561,12 +630,14 @@ FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t
         const Div32 dvh = q.dv_h[lvl];
         for (int p = threadIdx.x; p < len; p += blockDim.x) {
             const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-            if (lvl == q.P - 1) {
+            if (lvl == q.P - 1 && !MN) {
+                T[p] = pair_count<false>(q, (const int8_t*)nullptr, p);
+            } else if (lvl == q.P - 1) {
                 int32_t x0 = 0, y0 = 0;
                 const uint32_t c =
                     pair_xy<false>(q, (const int32_t*)nullptr, (const int32_t*)nullptr, p, x0, y0);
                 T[p] = c;
-                if (MN) {
+                {
                     if (c > 0) {
                         const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
                         MN[p] = min(l0, l1) - t;

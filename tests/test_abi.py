@@ -74,6 +74,21 @@ def test_enumerate_argument_validation():
     assert st == fs.FS_E_INVAL
 
 
+def test_cursor_and_host_enumerate_argument_validation():
+    L = fs.lib()
+    g = (ctypes.c_uint32 * 3)(3, 5, 7)
+    h = ctypes.c_void_p(0)
+    assert L.fs_cursor_create(100, g, 3, None, 3, None, ctypes.byref(h)) == fs.FS_E_INVAL
+    assert L.fs_cursor_create(100000, (ctypes.c_uint32 * 3)(1, 5, 7), 3, None, 2, None,
+                              ctypes.byref(h)) == fs.FS_E_OVERFLOW
+    assert L.fs_cursor_create(100, g, 3, None, 4, None, None) == fs.FS_E_INVAL
+    cnt = ctypes.c_uint64()
+    assert L.fs_enumerate_host(100, g, 3, None, None, 10, 4, ctypes.byref(cnt), None) == fs.FS_E_INVAL
+    assert L.fs_enumerate_host(100, g, 3, None, None, 0, 5, ctypes.byref(cnt), None) == fs.FS_E_INVAL
+    assert L.fs_cursor_next(None, None, 0, ctypes.byref(cnt), None) == fs.FS_E_INVAL
+    assert L.fs_cursor_seek(None, 0) == fs.FS_E_INVAL
+
+
 def test_predicate_validation():
     assert _status(fs.fs_any, 10, [3, 5], [1, 1], 3, 7) == fs.FS_E_INVAL  # op 7
     assert _status(fs.fs_any, 10, [3, 5], [1 << 21, 1], 3, 0) == fs.FS_E_INVAL
@@ -86,6 +101,12 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(fs.FsError) as e:
         fs.fs_count(500, [5, 7, 11, 13])
     assert e.value.status == fs.FS_E_CUDA
+    with pytest.raises(fs.FsError) as e:
+        fs.Cursor(500, [5, 7, 11, 13])
+    assert e.value.status == fs.FS_E_CUDA
+    with pytest.raises(fs.FsError) as e:
+        fs.Server()
+    assert e.value.status in (fs.FS_E_CUDA, fs.FS_E_NOMEM)
 
 
 @pytest.mark.parametrize("div", [1, 2, 3, 5, 7, 11, 13, 52, 56, 61, 100, 143, 728, 1000, 4093,
