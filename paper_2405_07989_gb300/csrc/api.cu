@@ -276,11 +276,6 @@ fs_config cfg_or_default(const fs_config* cfg)
     return c;
 }
 
-int method_of(const fs_config& c)
-{
-    return c.method == FS_METHOD_PLAIN ? FS_METHOD_PLAIN : FS_METHOD_PAIR;
-}
-
 // The query the trailing-k walk runs over: the first D-k levels as prefix
 // levels (k - 2 fewer than PAIR); the last k come from the trailing tables.
 // Enumerate counts its slices run by run from the trailing-three table (n + 1

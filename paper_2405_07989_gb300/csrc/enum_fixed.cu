@@ -2,26 +2,20 @@
 // the pair resolved through its tables, and the caller's column order equal to
 // the walk order or its reverse (generators given in descending or ascending
 // order).  A row's values are assembled in registers in caller order and
-// stored with fixed offsets (8-byte stores where the row is aligned); the
-// leaf of each row is found by a search over the warp's scan of row counts.
+// stored with fixed offsets (8-byte stores where the row is aligned).  Each
+// lane writes the rows of its own leaf, at the position the warp's scan of
+// row counts gives it: no row-to-leaf search and no shuffles per row (the
+// lanes of a chunk differ in row count by a few rows, so the divergent loop
+// stays short).  64 registers, four 256-thread blocks per SM.
 // Same results, layout and staging as the generic walk in enum.cu.
 #include "enum_common.cuh"
 #include "launch.h"
 
 namespace fsi {
 
-// Lane whose leaf holds row i of the chunk: the number of lanes whose
-// inclusive row count is <= i (the counts are non-decreasing over lanes).
-FS_D int leaf_of_row(uint32_t incl, uint32_t i)
-{
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t v = __shfl_sync(FULL, incl, lo + step - 1);
-        if (v <= i) lo += step;
-    }
-    return lo;
-}
+// A chunk whose leaves all have at most this many rows is written one lane per
+// leaf; otherwise leaf by leaf with all lanes.
+constexpr uint32_t LEAF_ROWS_MAX = 64;
 
 // PERM 1: caller column of level k is D-1-k; PERM 2: it is k.
 template <typename ELEM, int D, int PERM>
@@ -74,7 +68,9 @@ struct EnumFix {
         }
     }
 
-    // The rows of the leaf in lane `src` (rare, very many rows): all lanes.
+    // The rows of the leaf in lane `src`, all lanes together: for chunks with a
+    // leaf of more than LEAF_ROWS_MAX rows, where one lane per leaf would idle
+    // the others.
     FS_D void emit_one(const QueryConst& q, int lane, uint32_t cs, int32_t xs, int32_t ys,
                        int32_t as)
     {
@@ -98,7 +94,7 @@ struct EnumFix {
         int32_t x0 = 0, y0 = 0;
         uint32_t c = 0;
         if (valid) c = pair_xy<true>(q, X0, YD, r, x0, y0);
-        if (__any_sync(FULL, c > (uint32_t)ENUM_BIG)) {
+        if (__any_sync(FULL, c > (uint32_t)LEAF_ROWS_MAX)) {
             for (int src = 0; src < 32; src++) {
                 const uint32_t cs = __shfl_sync(FULL, c, src);
                 const int32_t xs = __shfl_sync(FULL, x0, src);
@@ -120,20 +116,11 @@ struct EnumFix {
             const uint32_t npc = min((uint32_t)piece, T - ps);
             if (!sg.fits((int)npc)) sg.flush();
             ELEM* sb = sg.cursor();
-            for (uint32_t j = 0; j < npc; j += 32) {
-                const uint32_t k = j + lane;
-                const bool ok = k < npc;
-                const uint32_t i = ok ? ps + k : T - 1;
-                const int src = leaf_of_row(incl, i);
-                const uint32_t es = __shfl_sync(FULL, excl, src);
-                const int32_t xs = __shfl_sync(FULL, x0, src);
-                const int32_t ys = __shfl_sync(FULL, y0, src);
-                const int32_t as = __shfl_sync(FULL, a, src);
-                if (ok) {
-                    const int32_t t = (int32_t)(i - es);
-                    put_row(sb + k * D, as, xs + t * q.v, ys - t * q.u);
-                }
-            }
+            // this lane's rows of the piece [ps, ps + npc): t = i - excl of its leaf
+            const uint32_t lo = max(excl, ps), hi = min(incl, ps + npc);
+            int32_t t = (int32_t)(lo - excl);
+            for (uint32_t i = lo; i < hi; i++, t++)
+                put_row(sb + (i - ps) * D, a, x0 + t * q.v, y0 - t * q.u);
             sg.nst += (int32_t)npc;
         }
         return false;
@@ -141,7 +128,7 @@ struct EnumFix {
 };
 
 template <typename ELEM, int D, int PERM>
-__global__ void __launch_bounds__(256, 3) k_pair_enum_fix(const __grid_constant__ QueryConst q,
+__global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant__ QueryConst q,
                                                           Scratch sc, int queue, ELEM* out,
                                                           uint64_t cap_rows)
 {
