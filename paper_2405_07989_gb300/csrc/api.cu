@@ -229,6 +229,26 @@ fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& c
     q.maxlen = (int32_t)(n / gmin);
     q.dbins = q.maxlen + std::abs(q.delta) + 1;
     q.nw = q.P - 1;
+    // common-divisor skipping for the pair walk (trailing gcd G) and for the
+    // trailing-three / trailing-four walks (gcd of the last three / four)
+    {
+        int64_t Gt = G;
+        for (int k = 0; k < 3; k++) {
+            const int inner = q.P - 1 - k;  // the walk's innermost level
+            if (k > 0) Gt = gcd64(Gt, q.h[q.P - k]);
+            int64_t g1 = 1, m = 1, inv = 0;
+            if (inner >= 0) {
+                g1 = gcd64(q.h[inner], Gt);
+                m = Gt / g1;
+                inv = m > 1 ? modinv((q.h[inner] / g1) % m, m) : 0;
+            }
+            q.sk_g[k] = (int32_t)g1;
+            q.sk_m[k] = (int32_t)m;
+            q.sk_inv[k] = (int32_t)inv;
+            q.dv_skg[k] = make_div32((uint32_t)g1);
+            q.dv_skm[k] = make_div32((uint32_t)m);
+        }
+    }
     // planner tables: nw * (n + 1) uint64
     const double wbytes = (double)q.nw * (double)(n + 1) * 8.0;
     if (wbytes > 8.0 * (1ull << 30))
@@ -518,14 +538,15 @@ fs_status prepare_device(Call& c, void* base)
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     {
         ProfScope ps("precompute", c.st,
-                     ((qw.tab_e || qw.tab_xy) ? 1 : 0) + (qw.nw > 0 ? 1 : 0) +
-                         ((triple || c.runs) ? 1 : 0));
-        e = launch_precompute(qw, c.sc, c.st);
+                     (qw.tab_e || qw.tab_xy || qw.nw > 0 || triple || c.runs) ? 1 : 0);
         const bool lens = op == OP_LEN;  // the length tables only where they are read
-        if (e == cudaSuccess && triple)
-            e = launch_trailing_tables(c.Q.q, c.trail, c.T3, lens ? c.MN3 : nullptr,
-                                       lens ? c.MX3 : nullptr, c.st);
-        if (e == cudaSuccess && c.runs) e = launch_trailing_tables(c.Q.q, 3, c.T3, nullptr, nullptr, c.st);
+        if (triple)
+            e = launch_precompute(qw, c.sc, c.st, &c.Q.q, c.trail, c.T3, lens ? c.MN3 : nullptr,
+                                  lens ? c.MX3 : nullptr);
+        else if (c.runs)
+            e = launch_precompute(qw, c.sc, c.st, &c.Q.q, 3, c.T3, nullptr, nullptr);
+        else
+            e = launch_precompute(qw, c.sc, c.st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
     {
@@ -564,16 +585,19 @@ cudaError_t call_walk(Call& c, Op op, int queue, const PredConst* pred, void* ou
 {
     if (c.method == FS_METHOD_TRIPLE) {
         ProfScope ps(walk_name(op, c.trail == 4 ? FS_METHOD_QUAD : FS_METHOD_TRIPLE), c.st, 1);
-        return launch_triple(c.q3, c.sc, op, c.lc, queue, c.T3, c.MN3, c.MX3, c.st);
+        return launch_triple(c.q3, c.sc, op, c.lc, queue, c.T3, c.MN3, c.MX3,
+                             op == OP_COUNT ? (uint64_t*)out : nullptr, c.st);
     }
     return launch_walk(c.Q.q, c.sc, op, c.method, c.lc, queue, pred, out, cap, eb, c.st);
 }
 
 fs_status do_count(Call& c, uint64_t* dev_count)
 {
-    cudaError_t e = call_walk(c, OP_COUNT, CTR_QUEUE, nullptr, nullptr, 0, 4);
+    // PAIR and trailing-table count walks copy the total to dev_count themselves
+    const bool walk_publishes = c.method != FS_METHOD_PLAIN;
+    cudaError_t e = call_walk(c, OP_COUNT, CTR_QUEUE, nullptr, walk_publishes ? dev_count : nullptr, 0, 4);
     if (e != cudaSuccess) return cuda_fail(e, "count launch");
-    if (dev_count) {
+    if (dev_count && !walk_publishes) {
         ProfScope ps("copy_result", c.st, 1);
         e = launch_copy_u64(c.sc.ctr + CTR_COUNT, dev_count, c.st);
         if (e != cudaSuccess) return cuda_fail(e, "copy launch");

@@ -163,6 +163,7 @@ struct BatchCons {
     uint32_t mn, mx;
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
+    static constexpr bool SKIP = false;
     FS_D void fault()
     {
         if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[BCTR_ERR], 1ull);

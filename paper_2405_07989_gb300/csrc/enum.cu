@@ -36,6 +36,7 @@ struct EnumCons {
     int32_t pre[NR];
 
     static constexpr int UNROLL = 1;
+    static constexpr bool SKIP = true;
     FS_D void fault() { flag_fault(ctr); }
 
     FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)

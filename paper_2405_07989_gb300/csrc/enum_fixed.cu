@@ -30,6 +30,7 @@ struct EnumFix {
     int32_t pre[NP > 0 ? NP : 1];
 
     static constexpr int UNROLL = 1;
+    static constexpr bool SKIP = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int, int32_t a2)
     {

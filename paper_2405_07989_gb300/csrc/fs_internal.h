@@ -89,6 +89,16 @@ struct QueryConst {
     int32_t maxlen;       // floor(n / min real g): the largest possible length
     int32_t dbins;        // histogram difference-array size: maxlen + |delta| + 1
     int32_t nw;           // number of leaf-weight tables: P - 1
+    // Common-divisor skipping (the congruence of Sec. 3.2.4 over the generators
+    // after the walk's innermost level): a leaf's residual R - a h_in must be a
+    // multiple of Gt, the gcd of those generators, for any completion to
+    // exist.  That holds iff sk_g = gcd(h_in, Gt) divides R and
+    // a = (R / sk_g) sk_inv (mod sk_m), sk_m = Gt / sk_g, sk_inv =
+    // (h_in / sk_g)^-1 mod sk_m; the walk visits only that class.  Index 0 is
+    // the walk's own query, 1 and 2 the trailing-three / trailing-four walks
+    // (reduce_to_trailing moves them to 0).  sk_g = sk_m = 1: nothing skipped.
+    int32_t sk_g[3], sk_m[3], sk_inv[3];
+    Div32 dv_skg[3], dv_skm[3];
     int32_t pad0;
 };
 
@@ -106,6 +116,7 @@ enum Ctr {
     CTR_TOTAL = 7,    // enumerate: total rows (from the scan)
     CTR_SEFF = 8,     // number of slices the planner chose
     CTR_L = 9,        // number of leaves
+    CTR_DONE = 10,    // blocks of a count walk that have added their part
     CTR_N = 16
 };
 

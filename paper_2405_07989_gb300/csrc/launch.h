@@ -18,7 +18,12 @@ struct LaunchCfg {
 };
 
 // tables.cu
-cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream_t st);
+// The walk query's tables (leaf counts, pair tables) and, with qt and
+// trail_k > 0, the trailing-k tables of qt (T, and MN / MX when not NULL):
+// one launch, one block per table.
+cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream_t st,
+                              const QueryConst* qt = nullptr, int trail_k = 0, uint64_t* T = nullptr,
+                              int32_t* MN = nullptr, int32_t* MX = nullptr);
 cudaError_t launch_scan_slices(const Scratch& sc, uint64_t* dev_count, cudaStream_t st);
 cudaError_t launch_len_finalize(const QueryConst& q, const Scratch& sc, uint64_t* hist, int s,
                                 cudaStream_t st);
@@ -40,7 +45,7 @@ cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const
                                    int blocks, cudaStream_t st);
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
                           int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
-                          cudaStream_t st);
+                          uint64_t* dev_count, cudaStream_t st);
 
 // enum_fixed.cu: the write walk specialised on the number of levels and a
 // caller-order / reversed column order; NULL when the query has neither.

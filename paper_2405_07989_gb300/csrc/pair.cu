@@ -20,6 +20,7 @@ struct CountCons {
     uint64_t total;  // this lane, all slices
     uint64_t* ctr;
     static constexpr int UNROLL = 4;
+    static constexpr bool SKIP = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -41,7 +42,7 @@ struct CountCons {
 
 template <bool TAB, bool PER_SLICE>
 __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ QueryConst q,
-                                                    Scratch sc, int queue)
+                                                    Scratch sc, int queue, uint64_t* dev_count)
 {
     __shared__ SmemQ sq;
     __shared__ unsigned long long bsum;
@@ -57,7 +58,10 @@ __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ Quer
     uint64_t v = warp_sum_u64(cons.total);
     if ((threadIdx.x & 31) == 0) atomicAdd(&bsum, (unsigned long long)v);
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&sc.ctr[CTR_COUNT], bsum);
+    if (threadIdx.x == 0) {
+        atomicAdd((unsigned long long*)&sc.ctr[CTR_COUNT], bsum);
+        publish_count(sc.ctr, dev_count);
+    }
 }
 
 // ===========================================================================
@@ -77,6 +81,7 @@ struct LenCons {
     uint32_t mn, mx;
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
+    static constexpr bool SKIP = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -199,6 +204,7 @@ struct AnyCons {
     int poll;
     uint64_t* ctr;
     static constexpr int UNROLL = 1;
+    static constexpr bool SKIP = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t a2)
     {
@@ -273,6 +279,7 @@ struct TripleCons {
     uint64_t acc, total;
     int32_t mn, mx;
     static constexpr int UNROLL = 4;
+    static constexpr bool SKIP = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -302,7 +309,8 @@ struct TripleCons {
 template <int MODE, bool PER_SLICE>
 __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ QueryConst q3,
                                                      Scratch sc, int queue, const uint64_t* T3,
-                                                     const int32_t* MN3, const int32_t* MX3)
+                                                     const int32_t* MN3, const int32_t* MX3,
+                                                     uint64_t* dev_count)
 {
     __shared__ SmemQ sq;
     __shared__ unsigned long long bsum;
@@ -331,12 +339,15 @@ __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ Que
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && bsum > 0) {
-        atomicAdd((unsigned long long*)&sc.ctr[CTR_COUNT], bsum);
-        if (MODE) {
-            atomicMax((unsigned long long*)&sc.ctr[CTR_MINC], (unsigned long long)(0xffffffffu - (uint32_t)bmin));
-            atomicMax((unsigned long long*)&sc.ctr[CTR_MAX], (unsigned long long)(uint32_t)bmax);
+    if (threadIdx.x == 0) {
+        if (bsum > 0) {
+            atomicAdd((unsigned long long*)&sc.ctr[CTR_COUNT], bsum);
+            if (MODE) {
+                atomicMax((unsigned long long*)&sc.ctr[CTR_MINC], (unsigned long long)(0xffffffffu - (uint32_t)bmin));
+                atomicMax((unsigned long long*)&sc.ctr[CTR_MAX], (unsigned long long)(uint32_t)bmax);
+            }
         }
+        publish_count(sc.ctr, dev_count);
     }
 }
 
@@ -380,13 +391,13 @@ cudaError_t triple_occupancy(int threads, int* nb)
 
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
                           int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
-                          cudaStream_t st)
+                          uint64_t* dev_count, cudaStream_t st)
 {
     const dim3 g(lc.blocks), b(lc.threads);
     switch (op) {
-    case OP_COUNT: k_triple_walk<0, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3); break;
-    case OP_SLICES: k_triple_walk<0, true><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3); break;
-    case OP_LEN: k_triple_walk<1, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3); break;
+    case OP_COUNT: k_triple_walk<0, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count); break;
+    case OP_SLICES: k_triple_walk<0, true><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
+    case OP_LEN: k_triple_walk<1, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -476,12 +487,12 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
     const bool tab = tab_for(q, op);
     const dim3 g(lc.blocks), b(lc.threads);
     switch (op) {
-    case OP_COUNT:
-        return tab ? go(k_pair_count<true, false>, g, b, smem, st, q, sc, queue)
-                   : go(k_pair_count<false, false>, g, b, smem, st, q, sc, queue);
+    case OP_COUNT:  // `out`: the device total (nullable)
+        return tab ? go(k_pair_count<true, false>, g, b, smem, st, q, sc, queue, (uint64_t*)out)
+                   : go(k_pair_count<false, false>, g, b, smem, st, q, sc, queue, (uint64_t*)out);
     case OP_SLICES:
-        return tab ? go(k_pair_count<true, true>, g, b, smem, st, q, sc, queue)
-                   : go(k_pair_count<false, true>, g, b, smem, st, q, sc, queue);
+        return tab ? go(k_pair_count<true, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr)
+                   : go(k_pair_count<false, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr);
     case OP_LEN:
         if (q.dbins <= 4096)
             return tab ? go(k_pair_len<true, true>, g, b, smem, st, q, sc, queue)

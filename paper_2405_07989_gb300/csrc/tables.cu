@@ -34,6 +34,48 @@ __global__ void __launch_bounds__(1024) k_weights(const __grid_constant__ QueryC
     }
 }
 
+// All per-query tables of a call in one launch, one role per block (the roles
+// are independent): the walk query's leaf counts W, its pair tables, and the
+// trailing-k tables of the original query.
+struct PrecompArgs {
+    QueryConst qw;  // the query the walk runs over
+    QueryConst qt;  // the query whose trailing tables are built (trail_k > 0)
+    uint64_t* W;
+    int8_t* E;
+    int32_t* X0;
+    int32_t* YD;
+    uint64_t* T;
+    int32_t* MN;
+    int32_t* MX;
+    int32_t trail_k;
+    int32_t nroles;
+    int32_t role[4];
+};
+enum { ROLE_WEIGHTS = 0, ROLE_PAIRTAB = 1, ROLE_TRAIL = 2 };
+
+__global__ void __launch_bounds__(1024) k_precompute(const __grid_constant__ PrecompArgs a)
+{
+    __shared__ uint64_t part64[1024];
+    __shared__ int32_t part32[1024];
+    switch (a.role[blockIdx.x]) {
+    case ROLE_WEIGHTS: {
+        const QueryConst& q = a.qw;
+        const int len = q.n + 1;
+        for (int k = q.P - 2; k >= 0; k--) {
+            const uint64_t* in = (k == q.P - 2) ? nullptr : a.W + (size_t)(k + 1) * len;
+            block_strided_prefix_sum(in, q.dv_in, a.W + (size_t)k * len, len, q.h[k], part64);
+        }
+        break;
+    }
+    case ROLE_PAIRTAB:
+        pair_tables_fill(a.qw, a.E, a.X0, a.YD, threadIdx.x, blockDim.x);
+        break;
+    case ROLE_TRAIL:
+        trailing_tables_block(a.qt, a.trail_k, a.T, a.MN, a.MX, part64, part32);
+        break;
+    }
+}
+
 // Leaf-count tables up to this size are staged in shared memory by the planner.
 constexpr size_t PLAN_SMEM_MAX = 160 * 1024;
 
@@ -231,17 +273,27 @@ cudaError_t launch_trailing_tables(const QueryConst& q, int k, uint64_t* T, int3
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream_t st)
+cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream_t st,
+                              const QueryConst* qt, int trail_k, uint64_t* T, int32_t* MN,
+                              int32_t* MX)
 {
-    if (q.tab_e || q.tab_xy) {
-        int threads = 256;
-        int blocks = (int)((q.lcm + threads - 1) / threads);
-        if (blocks > 1024) blocks = 1024;
-        k_pair_tables<<<blocks, threads, 0, st>>>(q, q.tab_e ? sc.E : nullptr,
-                                                  q.tab_xy ? sc.X0 : nullptr,
-                                                  q.tab_xy ? sc.YD : nullptr);
-    }
-    if (q.nw > 0) k_weights<<<1, 1024, 0, st>>>(q, sc.W);
+    PrecompArgs a;
+    memset(&a, 0, sizeof a);
+    a.qw = q;
+    if (qt) a.qt = *qt;
+    a.W = sc.W;
+    a.E = q.tab_e ? sc.E : nullptr;
+    a.X0 = q.tab_xy ? sc.X0 : nullptr;
+    a.YD = q.tab_xy ? sc.YD : nullptr;
+    a.T = T;
+    a.MN = MN;
+    a.MX = MX;
+    a.trail_k = trail_k;
+    if (q.nw > 0) a.role[a.nroles++] = ROLE_WEIGHTS;
+    if (q.tab_e || q.tab_xy) a.role[a.nroles++] = ROLE_PAIRTAB;
+    if (qt && trail_k > 0) a.role[a.nroles++] = ROLE_TRAIL;
+    if (a.nroles == 0) return cudaSuccess;
+    k_precompute<<<a.nroles, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
 

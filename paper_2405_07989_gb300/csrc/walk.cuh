@@ -297,6 +297,9 @@ FS_D int32_t warp_load_start(const QueryConst& q, const int32_t* hs, const int32
 // of sibling j, so the lex successor (a ballot over the levels) runs once per
 // group of siblings instead of once per run.  Cons must provide
 //   static constexpr int UNROLL   -- full 32-leaf steps per loop trip
+//   static constexpr bool SKIP    -- visit only the leaves that common-divisor
+//                                    skipping keeps (for consumers whose per-leaf
+//                                    work outweighs the per-run class arithmetic)
 //   void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)
 //       -- a new run starts (warp-uniform); its prefix is rp.a on lanes
 //          0..P-3 and a2 at level P-2 (rp.a of lane P-2 is stale);
@@ -308,6 +311,34 @@ FS_D int32_t warp_load_start(const QueryConst& q, const int32_t* hs, const int32
 //   void fault() -- the slice ran past the last leaf (a planner fault).
 // Returns true if the consumer stopped the walk.
 // ---------------------------------------------------------------------------
+// Common-divisor skipping for one run: of the leaves a = b .. b+nh-1 of a
+// run with residual R, only a = first + k ma (k < cnt) can have completions
+// (QueryConst::sk_*); cnt = 0 when R is not a multiple of sk_g.
+FS_D void skip_class(const QueryConst& q, uint32_t R, uint32_t b, uint32_t nh, uint32_t& first,
+                     uint32_t& cnt, uint32_t& ma)
+{
+    const uint32_t Rg = div32(R, q.dv_skg[0]);
+    if (Rg * (uint32_t)q.sk_g[0] != R) {
+        cnt = 0;
+        return;
+    }
+    const uint32_t m = (uint32_t)q.sk_m[0];
+    ma = m;
+    if (m == 1) return;  // every leaf of the run qualifies
+    const uint32_t rs = Rg - div32(Rg, q.dv_skm[0]) * m;  // Rg mod m
+    uint32_t as;                                          // the class: rs * inv mod m
+    if (m < 46341u) {  // the product stays below 2^31, the range of div32
+        const uint32_t p = rs * (uint32_t)q.sk_inv[0];
+        as = p - div32(p, q.dv_skm[0]) * m;
+    } else {
+        as = (uint32_t)(((uint64_t)rs * (uint64_t)(uint32_t)q.sk_inv[0]) % m);
+    }
+    const uint32_t bm = b - div32(b, q.dv_skm[0]) * m;  // b mod m
+    const uint32_t off = as >= bm ? as - bm : as + m - bm;
+    first = b + off;
+    cnt = off < nh ? div32(nh - 1 - off, q.dv_skm[0]) + 1 : 0;
+}
+
 template <class Cons>
 FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                      const int32_t* starts, uint64_t s, uint64_t nleaves, int lane, int32_t hk,
@@ -317,7 +348,7 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
     int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
     const int np = q.P - 1;
     const uint32_t hin = (uint32_t)hs[np];
-    const uint32_t step = 32u * hin;
+    const bool skip = q.sk_m[0] > 1 || q.sk_g[0] > 1;  // common-divisor skipping applies
     uint64_t rem = nleaves;
     for (;;) {
         // the current run (prefix of levels 0..P-2) and its siblings
@@ -335,34 +366,41 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
         for (uint32_t j = 0; j < nsib; j++) {
             const int32_t R = __shfl_sync(FULL, Rj, (int)j);
             const int32_t lp = lpc + (int32_t)j;
-            cons.run_begin(q, rp, lane, ac + (int32_t)j);
             const uint32_t len = div32((uint32_t)R, q.dv_in) + 1;
             const uint32_t left = len - (uint32_t)b;
             const uint32_t nh = rem < (uint64_t)left ? (uint32_t)rem : left;
-            // wrap-around arithmetic: lanes past the run end get a meaningless
-            // r and are masked
-            uint32_t a = (uint32_t)b + (uint32_t)lane;
-            uint32_t r = (uint32_t)R - a * hin;
-            const uint32_t full = nh >> 5;  // steps with every lane in the run
-            uint32_t i = 0;
-            if (Cons::UNROLL > 1) {
-                for (; i + Cons::UNROLL <= full; i += Cons::UNROLL) {
+            // the slice's leaves of this run are a = b .. b+nh-1; visit a = first
+            // + k ma, k < cnt (ma = 1: all of them)
+            uint32_t first = (uint32_t)b, cnt = nh, ma = 1;
+            if (Cons::SKIP && skip) skip_class(q, (uint32_t)R, (uint32_t)b, nh, first, cnt, ma);
+            if (cnt > 0) {
+                cons.run_begin(q, rp, lane, ac + (int32_t)j);
+                // wrap-around arithmetic: lanes past the run end get a
+                // meaningless r and are masked
+                const uint32_t astep = 32u * ma, step = astep * hin;
+                uint32_t a = first + (uint32_t)lane * ma;
+                uint32_t r = (uint32_t)R - a * hin;
+                const uint32_t full = cnt >> 5;  // steps with every lane in the run
+                uint32_t i = 0;
+                if (Cons::UNROLL > 1) {
+                    for (; i + Cons::UNROLL <= full; i += Cons::UNROLL) {
 #pragma unroll
-                    for (int u = 0; u < Cons::UNROLL; u++) {
-                        if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                        r -= step;
-                        a += 32;
+                        for (int u = 0; u < Cons::UNROLL; u++) {
+                            if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                            r -= step;
+                            a += astep;
+                        }
                     }
                 }
+                for (; i < full; i++) {
+                    if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                    r -= step;
+                    a += astep;
+                }
+                if (cnt & 31)
+                    if (cons.chunk(q, lane, (uint32_t)lane < (cnt & 31), (int32_t)r, (int32_t)a, lp))
+                        return true;
             }
-            for (; i < full; i++) {
-                if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                r -= step;
-                a += 32;
-            }
-            if (nh & 31)
-                if (cons.chunk(q, lane, (uint32_t)lane < (nh & 31), (int32_t)r, (int32_t)a, lp))
-                    return true;
             rem -= nh;
             if (rem == 0) return false;
             b = 0;
@@ -501,6 +539,20 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
         cons.slice_end(q, s);
         if (stop) break;
         s = __shfl_sync(FULL, nxt, 0);
+    }
+}
+
+// Called by thread 0 of every block of a count walk after it has added its
+// part to ctr[CTR_COUNT]: the last block to finish copies the total to
+// *dev_count (the caller's device memory), so no separate copy kernel runs.
+FS_D void publish_count(uint64_t* ctr, uint64_t* dev_count)
+{
+    if (!dev_count) return;
+    __threadfence();  // this block's addition is visible before its ticket
+    const unsigned long long t = atomicAdd((unsigned long long*)&ctr[CTR_DONE], 1ull);
+    if (t == gridDim.x - 1) {
+        __threadfence();
+        *dev_count = atomicAdd((unsigned long long*)&ctr[CTR_COUNT], 0ull);
     }
 }
 
@@ -670,6 +722,11 @@ FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t
 // The query the trailing-k walk runs over: k - 2 prefix levels fewer (in place).
 FS_HD void reduce_to_trailing(QueryConst& r, int k)
 {
+    r.sk_g[0] = r.sk_g[k - 2];
+    r.sk_m[0] = r.sk_m[k - 2];
+    r.sk_inv[0] = r.sk_inv[k - 2];
+    r.dv_skg[0] = r.dv_skg[k - 2];
+    r.dv_skm[0] = r.dv_skm[k - 2];
     r.D -= k - 2;
     r.P -= k - 2;
     r.dv_in = r.dv_h[r.P - 1];

@@ -111,3 +111,15 @@ def test_batch_matches_single_query_calls():
     got = fs.fs_batch_run(qs, fs.BATCH_LENGTHS)
     for (n, g), r in zip(qs, got):
         assert fs.fs_length_stats(n, g) == r[:3]
+
+
+@pytest.mark.parametrize("method", [fs.METHOD_PAIR, fs.METHOD_AUTO])
+def test_batch_common_divisors(method):
+    """Queries whose generators share divisors (the walks skip leaves and runs
+    that cannot complete) against the oracle."""
+    qs = [(97, (6, 10)), (240, (6, 10, 15)), (401, (4, 6, 8, 10)), (300, (12, 18, 27, 8)),
+          (420, (30, 42, 70, 105, 11)), (513, (2, 4, 6, 8, 10)), (512, (2, 4, 6, 8, 10)),
+          (900, (35, 21, 15, 9, 25, 49)), (1000, (100, 60, 36, 24, 18, 8, 12)),
+          (3000, (14, 21, 6, 10, 15, 35))]
+    cfg = fs.make_config(method=method)
+    assert fs.fs_batch_run(qs, fs.BATCH_LENGTHS, cfg) == expected(qs, fs.BATCH_LENGTHS)

@@ -492,3 +492,70 @@ def test_config3_other_seeds(seed):
     assert fs.fs_count(n, g) == oracle.count_dp(n, g)
     assert fs.fs_count(n, g, PAIR) == oracle.count_dp(n, g)
     assert fs.fs_count(n, g, TRIPLE) == oracle.count_dp(n, g)
+
+
+# ---------------------------------------------------------------------------
+# common-divisor skipping: generators that share divisors
+# ---------------------------------------------------------------------------
+DIVISOR_CASES = [(97, (6, 10)), (240, (6, 10, 15)), (401, (4, 6, 8, 10)), (300, (12, 18, 27, 8)),
+                 (420, (30, 42, 70, 105, 11)), (513, (2, 4, 6, 8, 10)), (512, (2, 4, 6, 8, 10)),
+                 (900, (35, 21, 15, 9, 25, 49)), (777, (14, 21, 6, 10, 15, 35)),
+                 (1000, (100, 60, 36, 24, 18, 8, 12)), (250, (5, 10, 15, 20, 25, 30)),
+                 (330, (22, 33, 55, 9, 6, 4))]
+
+
+@pytest.mark.parametrize("cfg", [PAIR, PAIR_KEEP, TRIPLE, QUAD, AUTO],
+                         ids=["pair", "pair_keep", "triple", "quad", "auto"])
+def test_common_divisor_counts_and_lengths(cfg):
+    """Walks that skip the leaves (and runs) whose residual cannot be a
+    multiple of the trailing generators' gcd give the exact counts and
+    length ranges."""
+    dmin = {id(TRIPLE): 4, id(QUAD): 5}.get(id(cfg), 1)
+    for n, g in DIVISOR_CASES:
+        if len(g) < dmin:
+            continue
+        assert fs.fs_count(n, g, cfg) == oracle.count_dp(n, g), (n, g)
+        mm = oracle.minmax_dp(n, g) or (0, 0)
+        assert fs.fs_length_stats(n, g, None, cfg) == (oracle.count_dp(n, g),) + tuple(mm), (n, g)
+
+
+@pytest.mark.parametrize("method", ["pair", "pair_keep"])
+def test_common_divisor_enumerate_histogram_any(method):
+    cfg = CONFIGS[method]
+    for n, g in DIVISOR_CASES:
+        rows = oracle.enumerate_sorted(n, g)
+        got, out = gpu_enumerate(n, g, cfg)
+        assert got == rows.shape[0]
+        d = len(g)
+        mine = out[:got * d].view(got, d).cpu().numpy() if got else np.zeros((0, d), np.int32)
+        if method == "pair_keep":
+            assert np.array_equal(mine, rows), (n, g)  # lex-ascending in the caller's order
+        else:
+            assert np.array_equal(lexsort_rows(mine), rows), (n, g)
+        hist = torch.zeros(oracle.hist_len(n, g), dtype=torch.int64, device="cuda")
+        fs.fs_length_stats(n, g, hist, cfg)
+        assert np.array_equal(hist.cpu().numpy().astype(np.uint64), oracle.length_dp(n, g)), (n, g)
+        w = [1] * d
+        for L in range(0, oracle.hist_len(n, g), 7):
+            assert fs.fs_any(n, g, w, L, cfg=cfg) == oracle.any_pred(n, g, w, L), (n, g, L)
+
+
+def test_common_divisor_slices_and_plain_agree():
+    """Per-slice counts with skipping equal the oracle's bounded streams, and
+    the PLAIN walk (no skipping) gives the same buffers."""
+    for n, g in DIVISOR_CASES[:6]:
+        for slices in (1, 5, 300):
+            order, bounds, leaves = fs.fs_plan(n, g, slices, PAIR)
+            counts = fs.fs_slice_counts(n, g, slices, PAIR)
+            wg = walk_gens(g, order)
+            for s_ in range(slices):
+                lo = bounds[s_]
+                if lo[0] < 0:
+                    assert counts[s_] == 0
+                    continue
+                hi = bounds[s_ + 1] if bounds[s_ + 1][0] >= 0 else None
+                c, _, _, _, _ = oracle.range_stats(n, wg, lo, hi, with_hist=False)
+                assert counts[s_] == c, (n, g, slices, s_)
+        a, oa = gpu_enumerate(n, g, PAIR)
+        b, ob = gpu_enumerate(n, g, PLAIN)
+        assert a == b and torch.equal(oa[:a * len(g)], ob[:b * len(g)])
