@@ -270,6 +270,13 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     assert int(dc[0]) == Z and int(dc[1]) == Z, (int(dc[0]), int(dc[1]), Z)
+    # host time to enqueue one step (the GPU idles between short kernels when
+    # this exceeds their device time)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        step()
+    host_ms = (time.perf_counter() - t0) / 5 * 1000.0
+    torch.cuda.synchronize()
 
     # ---- timed region: K steps, L2 flushed between steps (untimed) ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -364,7 +371,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "factorizations_per_step": Z,
                        "output_bytes": alg_bytes, "l2": "flushed between steps (256 MB write)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "breakdown": breakdown, "extras": extras,
+            "clocks": clk, "breakdown": breakdown, "host_enqueue_ms_per_step": host_ms,
+            "extras": extras,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(256) k_batch_walk(BatchDev b)
 
 cudaError_t batch_walk_occupancy(int mode, int threads, int* nb)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        nb, mode ? (const void*)k_batch_walk<1> : (const void*)k_batch_walk<0>, threads, 0);
+    return occupancy_cached(mode ? (const void*)k_batch_walk<1> : (const void*)k_batch_walk<0>,
+                            threads, 0, nb);
 }
 
 cudaError_t launch_batch(const BatchDev& b, int threads, int blocks, cudaStream_t st)

@@ -204,11 +204,7 @@ cudaError_t pair_enum_occupancy(const QueryConst& q, int threads, int elem_bytes
 {
     const void* k = enum_kernel(q, elem_bytes);
     const int smem = pair_enum_smem_bytes(q, threads, elem_bytes);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k, threads, smem);
+    return occupancy_cached(k, threads, smem, nb);
 }
 
 cudaError_t launch_pair_enum(const QueryConst& q, const Scratch& sc, const LaunchCfg& lc, int queue,
@@ -216,10 +212,8 @@ cudaError_t launch_pair_enum(const QueryConst& q, const Scratch& sc, const Launc
 {
     const void* k = enum_kernel(q, elem_bytes);
     const int smem = pair_enum_smem_bytes(q, lc.threads, elem_bytes);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = smem_optin(k, smem);
+    if (e != cudaSuccess) return e;
     QueryConst qq = q;
     Scratch ss = sc;
     int qu = queue;

@@ -7,6 +7,14 @@
 
 namespace fsi {
 
+// Launch attributes asked of the runtime once per device / kernel / shape
+// (hostcache.cu): blocks per SM, the dynamic shared-memory opt-in (a no-op up
+// to 48 KB), the SM count.
+cudaError_t occupancy_cached(const void* kern, int threads, int smem, int* nb);
+cudaError_t smem_optin(const void* kern, int smem);
+cudaError_t sm_count_cached(int* sms);
+
+
 enum Op { OP_COUNT = 0, OP_SLICES = 1, OP_LEN = 2, OP_ANY = 3, OP_ENUM = 4 };
 
 struct LaunchCfg {

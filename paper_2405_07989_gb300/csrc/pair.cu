@@ -386,7 +386,7 @@ cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const
 
 cudaError_t triple_occupancy(int threads, int* nb)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_triple_walk<1, false>, threads, 0);
+    return occupancy_cached((const void*)k_triple_walk<1, false>, threads, 0, nb);
 }
 
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
@@ -434,21 +434,15 @@ int pair_smem_bytes(const QueryConst& q, Op op, int threads, int elem_bytes)
 template <class K>
 static cudaError_t occ(K kern, int threads, int smem, int* nb)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, threads, smem);
+    return occupancy_cached((const void*)kern, threads, smem, nb);
 }
 
 template <typename... KArgs, typename... Args>
 static cudaError_t go(void (*kern)(KArgs...), dim3 g, dim3 b, int smem, cudaStream_t st,
                       Args... args)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = smem_optin((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
     kern<<<g, b, smem, st>>>(args...);
     return cudaGetLastError();
 }

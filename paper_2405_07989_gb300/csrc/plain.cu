@@ -341,10 +341,8 @@ template <typename... KArgs, typename... Args>
 static cudaError_t go(void (*kern)(KArgs...), dim3 g, dim3 b, int smem, cudaStream_t st,
                       Args... args)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = smem_optin((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
     kern<<<g, b, smem, st>>>(args...);
     return cudaGetLastError();
 }
@@ -394,9 +392,9 @@ cudaError_t launch_plain(const QueryConst& q, const Scratch& sc, Op op, const La
 cudaError_t plain_occupancy(const QueryConst& q, Op op, int threads, int* nb)
 {
     const int smem = plain_smem(q, op);
-    if (q.D <= 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<4, true>, threads, smem);
-    if (q.D <= 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<8, true>, threads, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_plain_count<16, true>, threads, smem);
+    if (q.D <= 4) return occupancy_cached((const void*)k_plain_count<4, true>, threads, smem, nb);
+    if (q.D <= 8) return occupancy_cached((const void*)k_plain_count<8, true>, threads, smem, nb);
+    return occupancy_cached((const void*)k_plain_count<16, true>, threads, smem, nb);
 }
 
 }  // namespace fsi

@@ -308,12 +308,9 @@ cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, 
 {
     const size_t wbytes = (size_t)q.nw * (size_t)(q.n + 1) * 8;
     if (wbytes > 0 && wbytes <= PLAN_SMEM_MAX && S_req >= 1024) {
-        int dev = 0, sms = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess && wbytes > 48 * 1024)
-            e = cudaFuncSetAttribute(k_plan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)wbytes);
+        int sms = 0;
+        cudaError_t e = sm_count_cached(&sms);
+        if (e == cudaSuccess) e = smem_optin((const void*)k_plan_smem, (int)wbytes);
         if (e != cudaSuccess) return e;
         const uint64_t need = (S_req + 31) / 32;  // blocks of 32 warps
         const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
