@@ -192,6 +192,31 @@ def cpu_oracle_run(pool, n, wg, budget_s: float = 30.0):
     return total, dt, done, len(tasks)
 
 
+def cpu_single_thread(n, wg, budget_s: float = 4.0):
+    """The oracle's bounded stream on one host thread over leading-coordinate
+    slices, lightest first, until the budget is spent: (factorizations,
+    seconds, slices).  And the exact count by the oracle's DP (not the
+    method: a coefficient of prod 1 / (1 - x^g_i)), timed alone."""
+    import oracle
+    d = len(wg)
+    top = n // wg[0]
+    t0 = time.perf_counter()
+    total = done = 0
+    for x in range(top, -1, -1):
+        lo = [x] + [0] * (d - 1)
+        hi = [x + 1] + [0] * (d - 1) if x < top else None
+        rows, _ = oracle.enumerate_range(n, wg, lo, hi)
+        total += int(rows.shape[0])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.count_dp(n, wg)
+    dp_s = time.perf_counter() - t1
+    return total, dt, done, dp_s
+
+
 def make_pool():
     import multiprocessing as mp
     cores = os.cpu_count() or 1
@@ -351,6 +376,7 @@ def run_gpu(args):
         extras = heavy_count_extras(fs, workloads, dev)
         extras["batched"] = batch_extras(fs, workloads, dev)
         extras["serving"] = serving_extras(fs, workloads, args.serve_rate, args.serve_requests)
+        extras["table1_context"] = table1_extras(fs, dev)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----
     cpu = None
@@ -359,10 +385,15 @@ def run_gpu(args):
         c, dt, done, ntask = cpu_oracle_run(pool, n, wg)
         pool.close()
         pool.join()
+        c1, dt1, done1, dp_s = cpu_single_thread(n, wg)
         cpu = {"value": c / dt, "unit": "factorizations/s", "cores": cores, "kind": "oracle",
                "sample": (f"{done}/{ntask} leading-coordinate slices of the same query "
                           f"({c} factorizations): oracle bounded streams, Algorithm 3.1, save "
-                          f"consumer, one slice per process ({cores} spawn processes)")}
+                          f"consumer, one slice per process ({cores} spawn processes)"),
+               "single_thread": {"value": c1 / dt1, "unit": "factorizations/s", "cores": 1,
+                                 "sample": f"{done1} leading-coordinate slices ({c1} factorizations)"},
+               "dp_count_seconds": dp_s,
+               "dp_note": "exact |Z| by the oracle's DP, one thread: not the method"}
 
     if rank == 0:
         line = {
@@ -446,6 +477,35 @@ def heavy_count_extras(fs, workloads, dev):
         "length_factorizations_per_s": Z / len_s,
         "length_min_max_only_s": len_minmax_s,
     }
+
+
+# The largest Table 1 cell per d, with the paper's best CUDA time (seconds,
+# RTX 3080 + Ryzen 3900X, whole-second resolution): context, not a target.
+TABLE1_CONTEXT = [(3, (13, 37, 38), 500000, 52), (4, (13, 37, 38, 40), 45000, 132),
+                  (5, (13, 37, 38, 40, 41), 9000, 131), (6, (13, 37, 38, 40, 41, 42), 3000, 335),
+                  (7, (13, 37, 38, 40, 41, 42, 43), 2000, 760)]
+
+
+def table1_extras(fs, dev):
+    """Materialise Z(n) for the largest Table 1 input of each d through the
+    synchronous C ABI (count, then enumerate into device memory), wall-clock
+    timed, beside the paper's own runtime for the same input."""
+    import torch
+    out = []
+    for d, g, n, paper_s in TABLE1_CONTEXT:
+        Z = fs.fs_count(n, g)
+        buf = torch.empty(max(Z, 1) * d, dtype=torch.int32, device=dev)
+        fs.fs_enumerate(n, g, buf, Z)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = fs.fs_count(n, g)
+        c2 = fs.fs_enumerate(n, g, buf, Z)
+        dt = time.perf_counter() - t0
+        assert c == Z and c2 == Z
+        out.append({"d": d, "n": n, "factorizations": Z, "seconds": dt,
+                    "paper_seconds_rtx3080": paper_s})
+        del buf
+    return out
 
 
 def batch_extras(fs, workloads, dev):

@@ -371,7 +371,7 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
 }
 
 struct Layout {
-    size_t ctr, W, E, X0, YD, cnt, off, D, starts, T3, MN3, MX3, extra, total;
+    size_t ctr, W, E, X0, YD, cnt, off, blk, D, starts, T3, MN3, MX3, extra, total;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -394,6 +394,8 @@ Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes, bool tri
     p = al(p + (size_t)S * 8);
     L.off = p;
     p = al(p + (size_t)(S + 1) * 8);
+    L.blk = p;
+    p = al(p + (size_t)(S / 32 + 2) * 8);
     L.D = p;
     p = al(p + (size_t)std::max(q.dbins, q.maxlen + 1) * 8);
     L.starts = p;
@@ -422,6 +424,7 @@ Scratch scratch_at(void* base, const Layout& L)
     s.YD = (int32_t*)(b + L.YD);
     s.slice_cnt = (uint64_t*)(b + L.cnt);
     s.slice_off = (uint64_t*)(b + L.off);
+    s.blk = nullptr;
     s.s_lo = 0;
     s.s_hi = ~0ull;
     s.row_lo = 0;
@@ -528,6 +531,7 @@ fs_status prepare_device(Call& c, void* base)
     const QueryConst& qw = c.wq();
     const Op op = c.op;
     c.sc = scratch_at(base, c.L);
+    if (c.runs) c.sc.blk = (uint64_t*)((char*)base + c.L.blk);
     if (triple || c.runs) {
         char* b = (char*)base;
         c.T3 = (uint64_t*)(b + c.L.T3);
@@ -610,12 +614,14 @@ fs_status enum_count_slices(Call& c, uint64_t* dev_count)
 {
     cudaError_t e;
     if (c.runs) {
+        // counts, offsets within groups of 32 slices, and (last block) the
+        // groups' offsets, in one launch
         ProfScope ps("pair_slice_runs", c.st, 1);
-        const uint64_t blocks = std::min<uint64_t>((c.lc.S + 7) / 8, 4096);
-        e = launch_pair_slice_runs(c.Q.q, c.sc, c.T3, (int)blocks, c.st);
-    } else {
-        e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
+        e = launch_pair_slice_runs(c.Q.q, c.sc, c.T3, c.lc.S, dev_count, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "enumerate count launch");
+        return FS_OK;
     }
+    e = launch_walk(c.Q.q, c.sc, OP_SLICES, c.method, c.lc, CTR_QUEUE, nullptr, nullptr, 0, 4, c.st);
     if (e != cudaSuccess) return cuda_fail(e, "enumerate count launch");
     {
         ProfScope ps("scan_slices", c.st, 1);
@@ -673,9 +679,15 @@ fs_status fetch_offsets(Call& c, uint64_t* S, uint64_t* total, std::vector<uint6
     *S = c.ds->pinned[CTR_SEFF];
     *total = c.ds->pinned[CTR_TOTAL];
     off.resize(*S + 1);
-    cudaError_t e = cudaMemcpyAsync(off.data(), c.sc.slice_off, (*S + 1) * 8, cudaMemcpyDeviceToHost, c.st);
+    std::vector<uint64_t> blk(c.sc.blk ? *S / 32 + 1 : 0);
+    cudaError_t e = cudaMemcpyAsync(off.data(), c.sc.slice_off, *S * 8, cudaMemcpyDeviceToHost, c.st);
+    if (e == cudaSuccess && c.sc.blk)
+        e = cudaMemcpyAsync(blk.data(), c.sc.blk, blk.size() * 8, cudaMemcpyDeviceToHost, c.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return cuda_fail(e, "slice offsets to host");
+    if (c.sc.blk)
+        for (uint64_t s = 0; s < *S; s++) off[s] += blk[s >> 5];
+    off[*S] = *total;
     return FS_OK;
 }
 

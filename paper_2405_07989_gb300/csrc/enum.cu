@@ -26,6 +26,7 @@ struct EnumCons {
     const int32_t* X0;
     const int32_t* YD;
     const uint64_t* slice_off;
+    const uint64_t* blk;
     uint8_t* map;          // row -> lane of its leaf, ENUM_MAPCAP entries
     int32_t* tmpl;         // MAXL = 16: the current run's prefix by level
     const int32_t* scol;   // MAXL = 16: column of each level
@@ -54,7 +55,10 @@ struct EnumCons {
         }
     }
 
-    FS_D void slice_begin(const QueryConst&, uint64_t s) { sg.begin(slice_off[s]); }
+    FS_D void slice_begin(const QueryConst&, uint64_t s)
+    {
+        sg.begin(slice_off[s] + (blk ? blk[s >> 5] : 0ull));
+    }
     FS_D void slice_end(const QueryConst&, uint64_t) { sg.flush(); }
 
     // Rows [excl, incl) of this chunk belong to this lane's leaf; T rows in all.
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(256, 3) k_pair_enum(const __grid_constant__ Qu
     cons.X0 = X0;
     cons.YD = YD;
     cons.slice_off = sc.slice_off;
+    cons.blk = sc.blk;
     cons.map = wp + 2 * ENUM_STG_BYTES;
     cons.tmpl = (int32_t*)(wp + 2 * ENUM_STG_BYTES + ENUM_MAPCAP);
     cons.scol = sq.col;

@@ -25,6 +25,7 @@ struct EnumFix {
     const int32_t* X0;
     const int32_t* YD;
     const uint64_t* slice_off;
+    const uint64_t* blk;
     uint64_t* ctr;
     int32_t piece;
     int32_t pre[NP > 0 ? NP : 1];
@@ -40,7 +41,10 @@ struct EnumFix {
             pre[k] = k == NP - 1 ? a2 : v;
         }
     }
-    FS_D void slice_begin(const QueryConst&, uint64_t s) { sg.begin(slice_off[s]); }
+    FS_D void slice_begin(const QueryConst&, uint64_t s)
+    {
+        sg.begin(slice_off[s] + (blk ? blk[s >> 5] : 0ull));
+    }
     FS_D void slice_end(const QueryConst&, uint64_t) { sg.flush(); }
 
     FS_D void put_row(ELEM* row, int32_t a, int32_t x, int32_t y) const
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant_
     cons.X0 = X0;
     cons.YD = YD;
     cons.slice_off = sc.slice_off;
+    cons.blk = sc.blk;
     cons.ctr = sc.ctr;
     cons.piece = (Stager<ELEM>::STG - Stager<ELEM>::VEC) / D;
 #pragma unroll

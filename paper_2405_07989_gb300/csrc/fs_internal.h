@@ -117,6 +117,8 @@ enum Ctr {
     CTR_SEFF = 8,     // number of slices the planner chose
     CTR_L = 9,        // number of leaves
     CTR_DONE = 10,    // blocks of a count walk that have added their part
+    CTR_SQ = 11,      // leaves per slice, floor(L / S) (planner)
+    CTR_SR = 12,      // L mod S: the first R slices have one leaf more (planner)
     CTR_N = 16
 };
 
@@ -127,7 +129,9 @@ struct Scratch {
     int32_t* X0;          // lcm
     int32_t* YD;          // lcm
     uint64_t* slice_cnt;  // S
-    uint64_t* slice_off;  // S + 1
+    uint64_t* slice_off;  // S + 1 row offsets; with blk: offsets within a group of 32 slices
+    uint64_t* blk;        // NULL, or the row offset of each group of 32 slices:
+                          // slice s starts at row blk[s / 32] + slice_off[s]
     uint64_t* D;          // dbins (global difference array)
     int32_t* starts;      // S * FS_MAX_D slice start states (planner output)
     // the window a walk covers: slices [s_lo, min(S, s_hi)); an enumerate

@@ -49,8 +49,11 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
 // pair.cu: the TRIPLE walk over the reduced query q3 (OP_COUNT, OP_SLICES,
 // OP_LEN = count + min / max length)
 cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
+// Enumerate's first walk, run by run (k_pair_slice_runs): per-slice counts,
+// the two-level offsets of Scratch::blk, the total (ctr[CTR_TOTAL] and, if
+// not NULL, *dev_count).  S_req: the planner's maximum slice count.
 cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
-                                   int blocks, cudaStream_t st);
+                                   uint64_t S_req, uint64_t* dev_count, cudaStream_t st);
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
                           int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
                           uint64_t* dev_count, cudaStream_t st);

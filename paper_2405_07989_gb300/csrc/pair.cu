@@ -353,34 +353,100 @@ __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ Que
 
 // Per-slice counts of PAIR slices from the trailing-three table, run by run
 // (slice_count_runs): the first walk of fs_enumerate when the table is cheap.
-// Slices are few thousand leaves each and take a handful of warp steps, so a
-// plain grid-stride over slices balances them.
-__global__ void __launch_bounds__(256) k_pair_slice_runs(const __grid_constant__ QueryConst q,
-                                                         Scratch sc, const uint64_t* T3)
+// Block b (32 warps) counts slices 32 b .. 32 b + 31, one per warp, and writes
+// their offsets within the group (slice_off) and the group total; the last
+// block to finish scans the group totals into blk (Scratch::blk), so the row
+// offsets need no separate scan over all slices.
+__global__ void __launch_bounds__(1024) k_pair_slice_runs(const __grid_constant__ QueryConst q,
+                                                          Scratch sc, const uint64_t* T3,
+                                                          uint64_t* dev_count)
 {
     __shared__ SmemQ sq;
+    __shared__ uint64_t wsum[32];
+    __shared__ bool last;
     load_smemq(q, sq);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
     const uint64_t S = sc.ctr[CTR_SEFF];
-    const SliceSplit split(sc.ctr[CTR_L], S);
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const SliceSplit split = planned_split(sc.ctr);
+    const uint64_t s = (uint64_t)blockIdx.x * 32 + w;
     bool fault = false;
-    for (uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+    uint64_t c = 0;
+    if (s < S) {
         const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
-        uint64_t c = 0;
         if (k1 > k0) c = slice_count_runs(q, sq.h, sq.dvh, sc.starts, s, k1 - k0, lane, hk, T3, &fault);
-        c = warp_sum_u64(c);
-        if (lane == 0) sc.slice_cnt[s] = c;
     }
+    c = warp_sum_u64(c);
     if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
+    if (lane == 0) {
+        wsum[w] = c;
+        if (s < S) sc.slice_cnt[s] = c;
+    }
+    __syncthreads();
+    if (w == 0) {  // offsets within the group, and the group's total
+        const uint64_t v = wsum[lane];
+        uint64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += t;
+        }
+        const uint64_t sl = (uint64_t)blockIdx.x * 32 + lane;
+        if (sl < S) sc.slice_off[sl] = x - v;
+        if (lane == 31) {
+            sc.blk[blockIdx.x] = x;
+            __threadfence();  // the total is visible before the ticket
+            const unsigned long long t = atomicAdd((unsigned long long*)&sc.ctr[CTR_DONE], 1ull);
+            last = t == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block: exclusive scan of the group totals (in place), the total
+    __threadfence();
+    const uint32_t nb = gridDim.x;
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < nb ? *(volatile uint64_t*)&sc.blk[i] : 0;
+        uint64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += t;
+        }
+        __syncthreads();  // wsum is free
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint64_t y = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(FULL, y, o);
+                if (lane >= o) y += t;
+            }
+            wsum[lane] = y;
+        }
+        __syncthreads();
+        if (i < nb) sc.blk[i] = carry + (w > 0 ? wsum[w - 1] : 0) + x - v;
+        carry += wsum[31];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the end of the last slice: row offset S = the total
+        if ((S & 31) == 0) sc.blk[S >> 5] = carry;
+        sc.slice_off[S] = carry - sc.blk[S >> 5];
+        sc.ctr[CTR_TOTAL] = carry;
+        if (dev_count) *dev_count = carry;
+    }
 }
 
 cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
-                                   int blocks, cudaStream_t st)
+                                   uint64_t S_req, uint64_t* dev_count, cudaStream_t st)
 {
-    k_pair_slice_runs<<<blocks, 256, 0, st>>>(q, sc, T3);
+    const unsigned blocks = (unsigned)((S_req + 31) / 32);
+    k_pair_slice_runs<<<blocks, 1024, 0, st>>>(q, sc, T3, dev_count);
     return cudaGetLastError();
 }
 

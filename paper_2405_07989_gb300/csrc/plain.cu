@@ -111,7 +111,7 @@ FS_D void plain_queue(const QueryConst& q, const SmemQP& sq, const Scratch& sc, 
 {
     const uint64_t S = sc.ctr[CTR_SEFF];
     const uint64_t L = sc.ctr[CTR_L];
-    const SliceSplit split(L, S);
+    const SliceSplit split = planned_split(sc.ctr);
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
     // thread t takes slice t first, then pops T, T+1, ... from the queue
@@ -239,7 +239,7 @@ struct PEnum {
     FS_D bool poll() { return false; }
     // the stream is lex-decreasing; rows go from the slice's end downwards so
     // that the buffer is lex-ascending, as with the PAIR method
-    FS_D void slice_begin(const Scratch& sc, uint64_t s) { row = sc.slice_off[s + 1]; }
+    FS_D void slice_begin(const Scratch& sc, uint64_t s) { row = slice_row0(sc, s + 1); }
     FS_D void slice_end(const Scratch&, uint64_t) {}
 };
 

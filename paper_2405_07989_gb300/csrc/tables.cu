@@ -93,14 +93,26 @@ FS_D void plan_slices(const QueryConst& q, const Scratch& sc, const uint64_t* W,
         if (want < 1) want = 1;
         if (want < S) S = want;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc.ctr[CTR_SEFF] = S;
-        sc.ctr[CTR_L] = L;
+    // one division per block, shared
+    __shared__ uint64_t sQ, sR;
+    if (threadIdx.x == 0) {
+        const SliceSplit sp(L, S);
+        sQ = sp.Q;
+        sR = sp.R;
+        if (blockIdx.x == 0) {
+            sc.ctr[CTR_SEFF] = S;
+            sc.ctr[CTR_L] = L;
+            sc.ctr[CTR_SQ] = sp.Q;
+            sc.ctr[CTR_SR] = sp.R;
+        }
     }
+    __syncthreads();
+    SliceSplit split;
+    split.Q = sQ;
+    split.R = sR;
     const int lane = threadIdx.x & 31;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const SliceSplit split(L, S);
     for (uint64_t s = gw; s < S; s += nw) {
         int32_t* st = sc.starts + s * START_W;
         const uint64_t k0 = split.start(s);

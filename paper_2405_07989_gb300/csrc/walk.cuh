@@ -24,9 +24,19 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---------------------------------------------------------------------------
 struct SliceSplit {
     uint64_t Q, R;
+    FS_HD SliceSplit() : Q(0), R(0) {}
     FS_HD SliceSplit(uint64_t L, uint64_t S) : Q(L / S), R(L % S) {}
     FS_HD uint64_t start(uint64_t s) const { return s * Q + (s < R ? s : R); }
 };
+
+// The planner's split, as it recorded it (no 64-bit division per thread).
+FS_D SliceSplit planned_split(const uint64_t* ctr)
+{
+    SliceSplit p;
+    p.Q = ctr[CTR_SQ];
+    p.R = ctr[CTR_SR];
+    return p;
+}
 
 FS_HD uint64_t slice_start(uint64_t s, uint64_t L, uint64_t S)
 {
@@ -524,7 +534,7 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
     const int lane = threadIdx.x & 31;
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
     const uint64_t S_all = sc.ctr[CTR_SEFF];
-    const SliceSplit split(sc.ctr[CTR_L], S_all);
+    const SliceSplit split = planned_split(sc.ctr);
     const uint64_t S = sc.s_hi < S_all ? sc.s_hi : S_all;  // the window's slices
     const uint64_t W = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
@@ -554,6 +564,12 @@ FS_D void publish_count(uint64_t* ctr, uint64_t* dev_count)
         __threadfence();
         *dev_count = atomicAdd((unsigned long long*)&ctr[CTR_COUNT], 0ull);
     }
+}
+
+// The first output row of slice s (see Scratch::blk).
+FS_D uint64_t slice_row0(const Scratch& sc, uint64_t s)
+{
+    return sc.slice_off[s] + (sc.blk ? sc.blk[s >> 5] : 0ull);
 }
 
 // Sets the device error flag the host checks after a synchronous call.
