@@ -7,8 +7,8 @@
 // shared memory, then one row per lane written into a shared-memory staging
 // buffer.  Full staging buffers are drained to global memory by the bulk-copy
 // engine (cp.async.bulk, 16-byte aligned body), the unaligned head and tail by
-// plain stores; two buffers per warp let the walk fill one while the other
-// drains.
+// plain stores; the warp waits for its copy to have read the buffer before
+// refilling it (other warps run meanwhile).
 #include "enum_common.cuh"
 #include "launch.h"
 
@@ -155,15 +155,14 @@ __global__ void __launch_bounds__(256, 3) k_pair_enum(const __grid_constant__ Qu
     cons.sg.cap_elems = cap_rows * (uint64_t)q.d;
     cons.sg.lo_elems = sc.row_lo * (uint64_t)q.d;
     cons.sg.wbase = wp;
-    cons.sg.buf = 0;
     cons.sg.d = q.d;
     cons.sg.begin(0);
     cons.X0 = X0;
     cons.YD = YD;
     cons.slice_off = sc.slice_off;
     cons.blk = sc.blk;
-    cons.map = wp + 2 * ENUM_STG_BYTES;
-    cons.tmpl = (int32_t*)(wp + 2 * ENUM_STG_BYTES + ENUM_MAPCAP);
+    cons.map = wp + ENUM_STG_BYTES;
+    cons.tmpl = (int32_t*)(wp + ENUM_STG_BYTES + ENUM_MAPCAP);
     cons.scol = sq.col;
     cons.ctr = sc.ctr;
     cons.np = q.P - 1;

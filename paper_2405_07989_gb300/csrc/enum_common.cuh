@@ -1,15 +1,15 @@
 // Shared pieces of the enumerate write walks (enum.cu, enum_fixed.cu): the
-// bulk-copy helpers and the per-warp double-buffered staging of rows.
+// bulk-copy helpers and the per-warp staging of rows.
 #pragma once
 
 #include "walk.cuh"
 
 namespace fsi {
 
-enum { ENUM_STG_BYTES = 3072, ENUM_MAPCAP = 256, ENUM_BIG = 1 << 26 };
-// per warp: two staging buffers, the row -> lane map, the run prefix of the
+enum { ENUM_STG_BYTES = 6144, ENUM_MAPCAP = 256, ENUM_BIG = 1 << 26 };
+// per warp: the staging buffer, the row -> lane map, the run prefix of the
 // generic (d > 8) path
-enum { ENUM_WARP_BYTES = 2 * ENUM_STG_BYTES + ENUM_MAPCAP + 2 * FS_MAX_D * 4 };
+enum { ENUM_WARP_BYTES = ENUM_STG_BYTES + ENUM_MAPCAP + 2 * FS_MAX_D * 4 };
 
 // --- bulk async copies, shared -> global (PTX cp.async.bulk, bulk groups) ---
 FS_D void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -22,8 +22,8 @@ FS_D void bulk_store(void* gdst, const void* ssrc, uint32_t bytes)
                  : "memory");
 }
 FS_D void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// at most one group still reading shared memory
-FS_D void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every group has read its shared memory (the source may be rewritten)
+FS_D void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // every group complete (writes performed)
 FS_D void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -42,12 +42,12 @@ struct Stager {
     ELEM* out;
     uint64_t cap_elems;
     uint64_t lo_elems;
-    unsigned char* wbase;  // this warp's two buffers
+    unsigned char* wbase;  // this warp's staging buffer
     uint64_t row_base;
-    int32_t buf, nst, phase, d;
+    int32_t nst, phase, d;
 
-    FS_D ELEM* stg(int k) const { return (ELEM*)(wbase + k * ENUM_STG_BYTES); }
-    FS_D ELEM* cursor() const { return stg(buf) + phase + nst * d; }
+    FS_D ELEM* stg() const { return (ELEM*)wbase; }
+    FS_D ELEM* cursor() const { return stg() + phase + nst * d; }
     FS_D bool fits(int rows) const { return phase + (nst + rows) * d <= STG; }
     // window position of the first staged element (negative: before the window)
     FS_D int64_t wpos() const { return (int64_t)(row_base * (uint64_t)d) - (int64_t)lo_elems; }
@@ -65,7 +65,7 @@ struct Stager {
         const int lane = threadIdx.x & 31;
         __syncwarp();  // every lane's staged rows are in place
         if (nst > 0) {
-            const ELEM* sb = stg(buf);
+            const ELEM* sb = stg();
             const int64_t e0 = wpos();
             const int64_t N = (int64_t)nst * d;
             const int64_t lo = e0 > 0 ? e0 : 0;
@@ -90,9 +90,10 @@ struct Stager {
                     }
                 }
             }
-            buf ^= 1;
-            // the buffer we switch to must no longer be read by its earlier copy
-            if (lane == 0) bulk_wait_read_1();
+            // one buffer per warp, reused at once: its copy must have read it.
+            // (Two half-size buffers, one filling while the other drains,
+            // flush twice as often and measured slower.)
+            if (lane == 0) bulk_wait_read_0();
             __syncwarp();
         }
         row_base += (uint64_t)nst;

@@ -155,7 +155,6 @@ __global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant_
     cons.sg.cap_elems = cap_rows * (uint64_t)D;
     cons.sg.lo_elems = sc.row_lo * (uint64_t)D;
     cons.sg.wbase = wp;
-    cons.sg.buf = 0;
     cons.sg.d = D;
     cons.sg.begin(0);
     cons.X0 = X0;
