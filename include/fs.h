@@ -52,7 +52,10 @@ typedef enum fs_status {
     FS_OK = 0,
     FS_E_INVAL = 1,     /* bad argument: d out of range, zero generator, n < 0, NULL pointer */
     FS_E_OVERFLOW = 2,  /* n + max g >= 2^31, int16 output that cannot hold a coordinate,
-                           or a planner table that would exceed its size limit */
+                           a planner table that would exceed its size limit, or a query
+                           whose count may reach 2^63: the bound
+                           (n + sum g)^(d-1) / ((d-1)! prod g) over the d-1 largest
+                           generators is checked before any work */
     FS_E_CAPACITY = 3,  /* enumerate: more factorizations than `cap` */
     FS_E_NOMEM = 4,     /* device scratch allocation failed */
     FS_E_CUDA = 5,      /* a CUDA runtime call or kernel launch failed; no device */

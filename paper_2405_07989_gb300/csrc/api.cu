@@ -3,6 +3,7 @@
 // consumer.  Every step of the computation runs in the kernels; this file
 // only validates, lays out memory and enqueues.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -175,6 +176,24 @@ fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& c
     }
     if (n + (int64_t)gmax > 2147483647LL)
         return fail(FS_E_OVERFLOW, "n + max g = %lld exceeds 2^31 - 1", (long long)(n + gmax));
+    // Counts and leaf counts are uint64.  Every factorization is fixed by its
+    // first d-1 coordinates (in any order), and each such prefix x with
+    // sum x_i g_i <= n owns the unit cube [x, x+1), which lies in the simplex
+    // sum y_i g_i <= n + sum g_i; so |Z| and the leaf counts are at most
+    //   (n + sum g_i)^(d-1) / ((d-1)! prod g_i)   (the d-1 largest generators).
+    // Queries whose bound reaches 2^63 are refused rather than risk a wrap.
+    if (d >= 2) {
+        std::vector<uint32_t> gs(gens, gens + d);
+        std::sort(gs.begin(), gs.end(), std::greater<uint32_t>());
+        long double lg = 0.0L, sum = 0.0L;
+        for (int i = 0; i < d - 1; i++) sum += gs[i];
+        for (int i = 0; i < d - 1; i++)
+            lg += logl(((long double)n + sum) / (long double)gs[i]) - logl((long double)(i + 1));
+        if (lg >= 63.0L * logl(2.0L))
+            return fail(FS_E_OVERFLOW,
+                        "the factorization count may exceed 2^63 (bound 2^%.1f): not representable",
+                        (double)(lg / logl(2.0L)));
+    }
     QueryConst& q = Q.q;
     memset(&q, 0, sizeof q);
     q.n = (int32_t)n;

@@ -74,6 +74,21 @@ def test_enumerate_argument_validation():
     assert st == fs.FS_E_INVAL
 
 
+def test_count_overflow_bound_refuses_before_gpu():
+    """Counts are uint64: a query whose count may reach 2^63 is refused up
+    front (the bound (n + sum g)^(d-1) / ((d-1)! prod g)); every workload of
+    the benchmarks and tests passes it."""
+    import oracle
+    from paper_2405_07989_gb300 import workloads
+    assert _status(fs.fs_count, 2**30, [1] * 8) == fs.FS_E_OVERFLOW
+    assert _status(fs.fs_count, 20000, [5, 6, 7, 8, 9, 10, 11, 12]) == fs.FS_E_OVERFLOW
+    assert oracle.count_dp(20000, (5, 6, 7, 8, 9, 10, 11, 12)) > 2**63  # rightly refused
+    ok = [workloads.config3(s) for s in range(3)] + [workloads.CONFIG1, workloads.CONFIG2]
+    ok += workloads.config4(0) + [(n, g) for _, _, n, g in workloads.config5(0, 2000, 1000.0, 20000)]
+    for n, g in ok:
+        assert _status(fs.fs_count, n, list(g)) != fs.FS_E_OVERFLOW, (n, g)
+
+
 def test_cursor_and_host_enumerate_argument_validation():
     L = fs.lib()
     g = (ctypes.c_uint32 * 3)(3, 5, 7)
