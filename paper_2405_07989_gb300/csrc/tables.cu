@@ -1,42 +1,39 @@
 // Per-query precompute and finalisation kernels.
 //
-//  k_pair_tables  the pair tables E / X0 / YD indexed by r mod lcm(A, B)
-//                 (closed form of the congruence step, Sec. 3.2.4)
-//  k_weights      the exact leaf counts W_k[p] that the slice planner unranks
-//                 (balanced division of labour, Sec. 4.1 and Sec. 6.2)
-//  k_plan         the slice planner: slice count and each slice's start state
+//  k_precompute   one block per table: the pair tables E / X0 / YD indexed by
+//                 r mod lcm(A, B) (closed form of the congruence step, Sec.
+//                 3.2.4), the exact leaf counts W_k[p] that the slice planner
+//                 unranks (balanced division of labour, Sec. 4.1 and 6.2), the
+//                 trailing-k tables (Sec. 6.1)
+//  k_plan(_smem)  the slice planner: slice count and each slice's start state
 //  k_scan_slices  exclusive scan of per-slice counts -> output offsets
 //  k_len_finalize histogram from the strided difference array
+//  k_copy_u64     a device counter to the caller's memory
 #include "launch.h"
 #include "walk.cuh"
 
 namespace fsi {
 
-// For w in [0, lcm): is w = x A + y B solvable with x, y >= 0 "within one
-// period", and where the solutions of r = q lcm + w start (see pair_count).
-__global__ void k_pair_tables(const __grid_constant__ QueryConst q, int8_t* E, int32_t* X0,
-                              int32_t* YD)
-{
-    pair_tables_fill(q, E, X0, YD, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-// W_k[p] = #{(a_k..a_{P-1}) >= 0 : sum_{i >= k} a_i h_i <= p} for k = 0..P-2,
-// p = 0..n.  W_k = W_{k+1} / (1 - x^{h_k}) as series, i.e. a strided prefix
-// sum; W_{P-1}[p] = floor(p / h_{P-1}) + 1 in closed form.  One block.
-__global__ void __launch_bounds__(1024) k_weights(const __grid_constant__ QueryConst q,
-                                                  uint64_t* W)
-{
-    __shared__ uint64_t part[1024];
-    const int len = q.n + 1;
-    for (int k = q.P - 2; k >= 0; k--) {
-        const uint64_t* in = (k == q.P - 2) ? nullptr : W + (size_t)(k + 1) * len;
-        block_strided_prefix_sum(in, q.dv_in, W + (size_t)k * len, len, q.h[k], part);
-    }
-}
-
 // All per-query tables of a call in one launch, one role per block (the roles
 // are independent): the walk query's leaf counts W, its pair tables, and the
 // trailing-k tables of the original query.
+//
+// Leaf counts: W_k[p] = #{(a_k..a_{P-1}) >= 0 : sum_{i >= k} a_i h_i <= p} for
+// k = 0..P-2, p = 0..n.  W_k = W_{k+1} / (1 - x^{h_k}) as series, i.e. a strided
+// prefix sum; W_{P-1}[p] = floor(p / h_{P-1}) + 1 in closed form.
+// Pair tables: for w in [0, lcm), whether w = x A + y B is solvable "within one
+// period" and where the solutions of r = q lcm + w start (see pair_count).
+// Trailing-k tables (Sec. 6.1: keep the factorizations of every small
+// residual over the trailing generators, here their count and length range).
+// For k = 3, with h = h_{P-1} and the pair (A, B) of q, for p = 0..n:
+//   T[p]  = #{(a, x, y) >= 0 : a h + x A + y B = p} = sum_{a >= 0} c2(p - a h)
+//   MN[p] = min of a + x + y over those solutions (TRIPLE_NONE if none)
+//   MX[p] = max of a + x + y (-TRIPLE_NONE if none)
+// c2 and the pair's length range come from the pair's closed form (its lengths
+// run l0 + t delta); the sums over a are strided scans: a running sum, and a
+// running min / max of (bound - floor(p/h)) plus floor(p/h).  k = 4 adds level
+// P-2 the same way: T4[p] = sum_{b >= 0} T3[p - b h_{P-2}], and so on for the
+// length range.  One block each.
 struct PrecompArgs {
     QueryConst qw;  // the query the walk runs over
     QueryConst qt;  // the query whose trailing tables are built (trail_k > 0)
@@ -255,32 +252,6 @@ __global__ void __launch_bounds__(1024) k_len_finalize(const __grid_constant__ Q
 }
 
 __global__ void k_copy_u64(const uint64_t* src, uint64_t* dst) { *dst = *src; }
-
-// Trailing-k tables (Sec. 6.1: keep the factorizations of every small
-// residual over the trailing generators, here their count and length range).
-// For k = 3, with h = h_{P-1} and the pair (A, B) of q, for p = 0..n:
-//   T[p]  = #{(a, x, y) >= 0 : a h + x A + y B = p} = sum_{a >= 0} c2(p - a h)
-//   MN[p] = min of a + x + y over those solutions (TRIPLE_NONE if none)
-//   MX[p] = max of a + x + y (-TRIPLE_NONE if none)
-// c2 and the pair's length range come from the pair's closed form (its lengths
-// run l0 + t delta); the sums over a are strided scans: a running sum, and a
-// running min / max of (bound - floor(p/h)) plus floor(p/h).  k = 4 adds level
-// P-2 the same way: T4[p] = sum_{b >= 0} T3[p - b h_{P-2}], and so on for the
-// length range.  One block.
-__global__ void __launch_bounds__(1024) k_trailing_tables(const __grid_constant__ QueryConst q, int k,
-                                                          uint64_t* T, int32_t* MN, int32_t* MX)
-{
-    __shared__ uint64_t part64[1024];
-    __shared__ int32_t part32[1024];
-    trailing_tables_block(q, k, T, MN, MX, part64, part32);
-}
-
-cudaError_t launch_trailing_tables(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
-                                   cudaStream_t st)
-{
-    k_trailing_tables<<<1, 1024, 0, st>>>(q, k, T, MN, MX);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // launchers
