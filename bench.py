@@ -1,13 +1,14 @@
 """Benchmark: factorizations/s on the single large query
 g = (11,13,17,19,23,29), n = 3000 (|Z| = 72,082,790; 1.73 GB of int32 rows).
 
-One step = the whole hot path over that query: fs_count (uint64 result) and
-fs_enumerate (all rows into a device buffer), i.e. precompute, planner,
-slice walks, consumers, finalisation.  `value` = |Z| per step / device time
-per step (inputs resident, results left on the device); `e2e` = the same
-through the synchronous C ABI with the rows copied back to pinned host memory
-inside the timed region.  The dominant kernel's roofline is the enumerate
-write walk against the measured HBM copy bandwidth.
+One step = the whole hot path over that query: fs_count (uint64 result, on a
+second stream beside the enumeration) and fs_enumerate (all rows into a device
+buffer), i.e. precompute, planner, slice walks, consumers, finalisation.
+`value` = |Z| per step / device time per step (inputs resident, results left
+on the device); `e2e` = the same through the synchronous C ABI (fs_count, and
+fs_enumerate_host streaming the rows into pinned host memory) inside the timed
+region.  The dominant kernel's roofline is the enumerate write walk against
+the measured HBM copy bandwidth.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -287,9 +288,16 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # the count and the enumeration are independent: the count runs on a
+    # second stream (each stream has its own library scratch) beside the
+    # enumeration's kernels; the step ends when both have finished
+    s_count = torch.cuda.Stream(dev)
+
     def step():
-        fs.fs_count_async(n, g, dc[0:1])
+        s_count.wait_stream(stream)
+        fs.fs_count_async(n, g, dc[0:1], stream=s_count.cuda_stream)
         fs.fs_enumerate_async(n, g, out, Z, dc[1:2])
+        stream.wait_stream(s_count)
 
     for _ in range(max(args.warmup, 3)):
         step()

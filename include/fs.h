@@ -24,11 +24,13 @@
  *            work is enqueued on it, in stream order with the caller's work.
  * - device memory passed in (dev_buf, hist_dev, dev_count) is owned by the
  *   caller and must be resident on the current device; the library never
- *   frees it.  The library owns only its internal scratch, which it allocates
- *   on first use per device, grows when needed and keeps until process exit.
- *   Calls that share a device share that scratch: the library serialises them
- *   on the host, and asynchronous calls on DIFFERENT streams of one device must
- *   not overlap on the GPU (order them with events or one stream).
+ *   frees it.  The library owns only its internal scratch: one arena per
+ *   (device, stream handle), allocated on first use, grown when needed and
+ *   kept until process exit.  Calls on one stream are ordered by it; calls on
+ *   different streams use different arenas and may overlap on the GPU.  (A
+ *   stream handle that is destroyed and later reused by the runtime inherits
+ *   its arena: destroy a stream only after its library work has completed.)
+ *   Host-side entry is serialised by the library.
  * - synchronous calls (no _async suffix) return after their host outputs are
  *   written; they synchronise `stream`.
  * - errors: every call returns an fs_status and writes its outputs only on
@@ -332,10 +334,11 @@ fs_status fs_batch_run(const fs_query* queries, int nq, int mode, const fs_confi
 fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config* best,
                             double* best_ms, void* stream);
 
-/* Grows the library's per-device scratch to at least `bytes` now (it is
- * otherwise grown on demand, which synchronises the device).  Call before
- * stream capture or before a latency-sensitive loop. */
-fs_status fs_reserve(uint64_t bytes);
+/* Grows the scratch of `stream` on the current device to at least `bytes`
+ * now (it is otherwise grown on demand, which waits for the stream's earlier
+ * work and frees the old scratch).  Call before stream capture or before a
+ * latency-sensitive loop. */
+fs_status fs_reserve(uint64_t bytes, void* stream);
 
 /* --- serving: a request loop with continuous batching -------------------- */
 
@@ -354,9 +357,8 @@ fs_status fs_reserve(uint64_t bytes);
  * fs_server_release.  Results are exactly those of the single-query calls.
  * A single query whose tables exceed table_bytes is answered FS_E_CAPACITY.
  * Thread safety: submit / poll / release may be called from any thread.
- * The server uses the library's shared per-device scratch for its enumerates:
- * do not run other asynchronous library calls on the same device while it
- * lives, unless ordered after fs_server_destroy. */
+ * The server's batches own their memory and its enumerates run on a stream
+ * of its own, so other library calls may run beside it. */
 enum { FS_REQ_COUNT = 0, FS_REQ_LENGTHS = 1, FS_REQ_ENUMERATE = 2 };
 
 typedef struct fs_server_config {

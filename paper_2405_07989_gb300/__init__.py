@@ -139,7 +139,7 @@ SIGNATURES = {
     "fs_batch_load": (ctypes.c_int, [_vp, ctypes.POINTER(fs_query), ctypes.c_int, _vp]),
     "fs_batch_fetch": (ctypes.c_int, [_vp, _vp]),
     "fs_batch_collect": (ctypes.c_int, [_vp, ctypes.POINTER(fs_result)]),
-    "fs_reserve": (ctypes.c_int, [ctypes.c_uint64]),
+    "fs_reserve": (ctypes.c_int, [ctypes.c_uint64, _vp]),
     "fs_server_create": (ctypes.c_int, [ctypes.POINTER(fs_server_config),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "fs_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(fs_request), _u64p]),
@@ -463,9 +463,10 @@ class Batch:
             pass
 
 
-def fs_reserve(nbytes: int) -> None:
-    """Grow the library's per-device scratch to at least nbytes now."""
-    _check(lib().fs_reserve(int(nbytes)))
+def fs_reserve(nbytes: int, stream=None) -> None:
+    """Grow the scratch of `stream` (default: torch's current stream) to at
+    least nbytes now."""
+    _check(lib().fs_reserve(int(nbytes), _stream(stream)))
 
 
 class Server:

@@ -40,9 +40,14 @@ fs_status cuda_fail(cudaError_t e, const char* where)
 // ---------------------------------------------------------------------------
 // per-device state: scratch arena and a pinned result buffer
 // ---------------------------------------------------------------------------
-struct DevState {
-    void* arena = nullptr;
+// Scratch of the calls on one stream of a device.
+struct Arena {
+    void* p = nullptr;
     size_t size = 0;
+};
+
+struct DevState {
+    std::map<cudaStream_t, Arena> arenas;  // one scratch arena per stream
     uint64_t* pinned = nullptr;
     int sms = 0;
     // fs_enumerate_host: two device staging buffers, a copy stream, events
@@ -76,24 +81,32 @@ fs_status get_dev(DevState** out)
     return FS_OK;
 }
 
-fs_status ensure_arena(DevState* ds, size_t bytes)
+// The scratch arena of `st` on this device, at least `bytes` long.  Calls on
+// one stream are ordered by it, so they can share its arena; calls on
+// different streams have separate arenas and may overlap on the GPU.
+fs_status ensure_arena(DevState* ds, cudaStream_t st, size_t bytes, void** out)
 {
-    if (ds->size >= bytes) return FS_OK;
-    if (ds->arena) {
-        cudaDeviceSynchronize();  // earlier work may still use the old arena
-        cudaFree(ds->arena);
-        ds->arena = nullptr;
-        ds->size = 0;
+    Arena& a = ds->arenas[st];
+    if (a.size >= bytes) {
+        *out = a.p;
+        return FS_OK;
+    }
+    if (a.p) {
+        cudaStreamSynchronize(st);  // earlier work on this stream may still use it
+        cudaFree(a.p);
+        a.p = nullptr;
+        a.size = 0;
     }
     size_t want = std::max(bytes, (size_t)16 << 20);
     want = (want + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
-    cudaError_t e = cudaMalloc(&ds->arena, want);
+    cudaError_t e = cudaMalloc(&a.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        ds->arena = nullptr;
+        a.p = nullptr;
         return fail(FS_E_NOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
     }
-    ds->size = want;
+    a.size = want;
+    *out = a.p;
     return FS_OK;
 }
 
@@ -586,9 +599,10 @@ fs_status prepare(Call& c, int64_t n, const uint32_t* gens, int d, const fs_conf
 {
     fs_status s = prepare_host(c, n, gens, d, cfg, op, eb, stream, extra_bytes, lengths_only);
     if (s != FS_OK) return s;
-    s = ensure_arena(c.ds, c.L.total);
+    void* arena = nullptr;
+    s = ensure_arena(c.ds, c.st, c.L.total, &arena);
     if (s != FS_OK) return s;
-    return prepare_device(c, c.ds->arena);
+    return prepare_device(c, arena);
 }
 
 fs_status read_ctr(Call& c)
@@ -1175,13 +1189,14 @@ fs_status fs_slice_counts(int64_t n, const uint32_t* gens, int d, const fs_confi
     return FS_OK;
 }
 
-fs_status fs_reserve(uint64_t bytes)
+fs_status fs_reserve(uint64_t bytes, void* stream)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     DevState* ds = nullptr;
     fs_status s = get_dev(&ds);
     if (s != FS_OK) return s;
-    return ensure_arena(ds, (size_t)bytes);
+    void* arena = nullptr;
+    return ensure_arena(ds, (cudaStream_t)stream, (size_t)bytes, &arena);
 }
 
 void fs_profile_enable(int on)

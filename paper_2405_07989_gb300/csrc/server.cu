@@ -311,7 +311,6 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&s->dev);
     fs_status st = e == cudaSuccess ? FS_OK : FS_E_CUDA;
-    if (st == FS_OK) st = fs_reserve(64ull << 20);
     for (int i = 0; st == FS_OK && i < s->cfg.slots; i++) {
         Slot sl;
         st = fs_batch_reserve(s->cfg.max_batch, s->cfg.table_bytes, FS_BATCH_LENGTHS, nullptr, &sl.b);
@@ -327,6 +326,7 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
             cudaStreamCreateWithFlags(&s->enum_st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->enum_ev, cudaEventDisableTiming) != cudaSuccess)
             st = FS_E_NOMEM;
+        if (st == FS_OK) st = fs_reserve(64ull << 20, s->enum_st);  // the enumerates' scratch
         s->pool.size = s->cfg.mem_budget_bytes;
         s->pool.free_blocks[0] = s->cfg.mem_budget_bytes;
     }
