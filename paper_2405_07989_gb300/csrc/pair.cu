@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ Que
 // their offsets within the group (slice_off) and the group total; the last
 // block to finish scans the group totals into blk (Scratch::blk), so the row
 // offsets need no separate scan over all slices.
-__global__ void __launch_bounds__(1024) k_pair_slice_runs(const __grid_constant__ QueryConst q,
+__global__ void __launch_bounds__(1024, 2) k_pair_slice_runs(const __grid_constant__ QueryConst q,
                                                           Scratch sc, const uint64_t* T3,
                                                           uint64_t* dev_count)
 {

@@ -154,7 +154,18 @@ __global__ void __launch_bounds__(1024) k_plan_smem(const __grid_constant__ Quer
     const uint32_t words = (uint32_t)q.nw * (uint32_t)(q.n + 1);
     const ulonglong2* src = (const ulonglong2*)sc.W;  // 256-byte aligned section
     ulonglong2* dst = (ulonglong2*)Ws;
-    for (uint32_t i = threadIdx.x; i < words / 2; i += blockDim.x) dst[i] = src[i];
+    // four independent 16-byte loads in flight per thread before their stores:
+    // one block's copy is bound by the loads it keeps outstanding
+    const uint32_t n2 = words / 2, bd = blockDim.x;
+    for (uint32_t i = threadIdx.x; i < n2; i += 4 * bd) {
+        ulonglong2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (i + k * bd < n2) v[k] = src[i + k * bd];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (i + k * bd < n2) dst[i + k * bd] = v[k];
+    }
     if ((words & 1) && threadIdx.x == 0) Ws[words - 1] = sc.W[words - 1];
     __syncthreads();
     plan_slices(q, sc, Ws, hs, dvh, S_req, auto_s, min_leaves);
@@ -295,7 +306,7 @@ cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, 
         cudaError_t e = sm_count_cached(&sms);
         if (e == cudaSuccess) e = smem_optin((const void*)k_plan_smem, (int)wbytes);
         if (e != cudaSuccess) return e;
-        const uint64_t need = (S_req + 31) / 32;  // blocks of 32 warps
+        const uint64_t need = (S_req + 31) / 32;  // blocks of 32 warps, one per SM
         const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
         k_plan_smem<<<blocks, 1024, wbytes, st>>>(q, sc, S_req, auto_s, min_leaves);
         return cudaGetLastError();
