@@ -333,6 +333,9 @@ fs_config cfg_or_default(const fs_config* cfg)
 // Enumerate counts its slices run by run from the trailing-three table (n + 1
 // uint64 entries) below this n, leaf by leaf above it.
 constexpr int32_t RUNS_MAX_N = 1 << 20;
+// ... and builds that table and the leaf counts in each planner block's shared
+// memory (one launch for tables, planner and counts) while they fit in this.
+constexpr size_t PLAN_RUNS_SMEM_MAX = 200 * 1024;
 
 // Trailing levels the tables can take for q under `method` (0: none).
 // k = 3 needs D >= 4 (one prefix level left) and n < 2^27 (the length
@@ -427,7 +430,7 @@ Layout make_layout(const QueryConst& q, uint64_t S, size_t extra_bytes, bool tri
     L.off = p;
     p = al(p + (size_t)(S + 1) * 8);
     L.blk = p;
-    p = al(p + (size_t)(S / 32 + 2) * 8);
+    p = al(p + (size_t)(S / SLICE_GROUP + 2) * 8);
     L.D = p;
     p = al(p + (size_t)std::max(q.dbins, q.maxlen + 1) * 8);
     L.starts = p;
@@ -495,6 +498,7 @@ struct Call {
     int method = FS_METHOD_PAIR;  // PLAIN, PAIR, or TRIPLE for the trailing-k tables
     int trail = 0;                // TRIPLE: k = 3 or 4 trailing levels in the tables
     bool runs = false;            // PAIR enumerate: per-slice counts run by run from T3
+    bool fused = false;           // runs, with tables, planner and counts in one launch
     Op op = OP_COUNT;
     DevState* ds = nullptr;
     Scratch sc;
@@ -542,6 +546,7 @@ fs_status prepare_host(Call& c, int64_t n, const uint32_t* gens, int d, const fs
     // enumerate's first walk (per-slice counts) goes run by run over the
     // trailing-three table when the table is small
     c.runs = op == OP_ENUM && c.method == FS_METHOD_PAIR && c.Q.q.n < RUNS_MAX_N;
+    c.fused = c.runs && plan_runs_smem_bytes(c.Q.q) <= PLAN_RUNS_SMEM_MAX;
     const QueryConst& qw = c.wq();
     s = get_dev(&c.ds);
     if (s != FS_OK) return s;
@@ -572,6 +577,7 @@ fs_status prepare_device(Call& c, void* base)
     }
     cudaError_t e = cudaMemsetAsync(c.sc.ctr, 0, CTR_N * 8, c.st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (c.fused) return FS_OK;  // tables and planner run inside enum_count_slices
     {
         ProfScope ps("precompute", c.st,
                      (qw.tab_e || qw.tab_xy || qw.nw > 0 || triple || c.runs) ? 1 : 0);
@@ -646,8 +652,14 @@ fs_status do_count(Call& c, uint64_t* dev_count)
 fs_status enum_count_slices(Call& c, uint64_t* dev_count)
 {
     cudaError_t e;
+    if (c.fused) {
+        ProfScope ps("plan_runs", c.st, 1);
+        e = launch_plan_runs(c.Q.q, c.sc, c.lc.S, c.lc.auto_s, c.lc.min_leaves, dev_count, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "enumerate plan launch");
+        return FS_OK;
+    }
     if (c.runs) {
-        // counts, offsets within groups of 32 slices, and (last block) the
+        // counts, offsets within groups of slices, and (last block) the
         // groups' offsets, in one launch
         ProfScope ps("pair_slice_runs", c.st, 1);
         e = launch_pair_slice_runs(c.Q.q, c.sc, c.T3, c.lc.S, dev_count, c.st);
@@ -712,14 +724,14 @@ fs_status fetch_offsets(Call& c, uint64_t* S, uint64_t* total, std::vector<uint6
     *S = c.ds->pinned[CTR_SEFF];
     *total = c.ds->pinned[CTR_TOTAL];
     off.resize(*S + 1);
-    std::vector<uint64_t> blk(c.sc.blk ? *S / 32 + 1 : 0);
+    std::vector<uint64_t> blk(c.sc.blk ? *S / SLICE_GROUP + 1 : 0);
     cudaError_t e = cudaMemcpyAsync(off.data(), c.sc.slice_off, *S * 8, cudaMemcpyDeviceToHost, c.st);
     if (e == cudaSuccess && c.sc.blk)
         e = cudaMemcpyAsync(blk.data(), c.sc.blk, blk.size() * 8, cudaMemcpyDeviceToHost, c.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return cuda_fail(e, "slice offsets to host");
     if (c.sc.blk)
-        for (uint64_t s = 0; s < *S; s++) off[s] += blk[s >> 5];
+        for (uint64_t s = 0; s < *S; s++) off[s] += blk[s / SLICE_GROUP];
     off[*S] = *total;
     return FS_OK;
 }

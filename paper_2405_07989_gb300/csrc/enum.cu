@@ -57,7 +57,7 @@ struct EnumCons {
 
     FS_D void slice_begin(const QueryConst&, uint64_t s)
     {
-        sg.begin(slice_off[s] + (blk ? blk[s >> 5] : 0ull));
+        sg.begin(slice_off[s] + (blk ? blk[s / SLICE_GROUP] : 0ull));
     }
     FS_D void slice_end(const QueryConst&, uint64_t) { sg.flush(); }
 

@@ -105,6 +105,10 @@ struct QueryConst {
 // ---------------------------------------------------------------------------
 // Device scratch layout of one call (byte offsets into the scratch arena).
 // ---------------------------------------------------------------------------
+// Slices counted per block when enumerate's first walk goes run by run (the
+// groups of Scratch::blk).
+constexpr int SLICE_GROUP = 256;
+
 enum Ctr {
     CTR_QUEUE = 0,    // slice queue head (first walk)
     CTR_QUEUE2 = 1,   // slice queue head (second walk)
@@ -130,8 +134,8 @@ struct Scratch {
     int32_t* YD;          // lcm
     uint64_t* slice_cnt;  // S
     uint64_t* slice_off;  // S + 1 row offsets; with blk: offsets within a group of 32 slices
-    uint64_t* blk;        // NULL, or the row offset of each group of 32 slices:
-                          // slice s starts at row blk[s / 32] + slice_off[s]
+    uint64_t* blk;        // NULL, or the row offset of each group of SLICE_GROUP
+                          // slices: slice s starts at row blk[s / SLICE_GROUP] + slice_off[s]
     uint64_t* D;          // dbins (global difference array)
     int32_t* starts;      // S * FS_MAX_D slice start states (planner output)
     // the window a walk covers: slices [s_lo, min(S, s_hi)); an enumerate

@@ -19,9 +19,12 @@ std::map<std::pair<int, const void*>, int> g_optin;
 std::map<int, int> g_sms;
 }  // namespace
 
+// The opt-in covers the kernel's static shared memory too: static + dynamic
+// above 48 KB needs it even when the dynamic part alone is below, so every
+// nonzero dynamic size is declared (once per device, kernel and larger size).
 cudaError_t smem_optin(const void* kern, int smem)
 {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem <= 0) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

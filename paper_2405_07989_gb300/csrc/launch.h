@@ -8,8 +8,8 @@
 namespace fsi {
 
 // Launch attributes asked of the runtime once per device / kernel / shape
-// (hostcache.cu): blocks per SM, the dynamic shared-memory opt-in (a no-op up
-// to 48 KB), the SM count.
+// (hostcache.cu): blocks per SM, the dynamic shared-memory opt-in, the SM
+// count.
 cudaError_t occupancy_cached(const void* kern, int threads, int smem, int* nb);
 cudaError_t smem_optin(const void* kern, int smem);
 cudaError_t sm_count_cached(int* sms);
@@ -50,6 +50,11 @@ cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
 // Enumerate's first walk, run by run (k_pair_slice_runs): per-slice counts,
 // the two-level offsets of Scratch::blk, the total (ctr[CTR_TOTAL] and, if
 // not NULL, *dev_count).  S_req: the planner's maximum slice count.
+// The planner and enumerate's run-level counts in one launch, the tables in
+// shared memory (k_plan_runs); usable when plan_runs_smem_bytes(q) fits.
+size_t plan_runs_smem_bytes(const QueryConst& q);
+cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
+                             uint64_t min_leaves, uint64_t* dev_count, cudaStream_t st);
 cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
                                    uint64_t S_req, uint64_t* dev_count, cudaStream_t st);
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,

@@ -353,15 +353,15 @@ __global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ Que
 
 // Per-slice counts of PAIR slices from the trailing-three table, run by run
 // (slice_count_runs): the first walk of fs_enumerate when the table is cheap.
-// Block b (32 warps) counts slices 32 b .. 32 b + 31, one per warp, and writes
-// their offsets within the group (slice_off) and the group total; the last
-// block to finish scans the group totals into blk (Scratch::blk), so the row
-// offsets need no separate scan over all slices.
-__global__ void __launch_bounds__(1024, 2) k_pair_slice_runs(const __grid_constant__ QueryConst q,
+// Block b counts the SLICE_GROUP slices from b * SLICE_GROUP on (each warp 8
+// consecutive ones) and group_offsets turns the counts into row offsets, so
+// no separate scan over all slices runs.
+__global__ void __launch_bounds__(1024) k_pair_slice_runs(const __grid_constant__ QueryConst q,
                                                           Scratch sc, const uint64_t* T3,
                                                           uint64_t* dev_count)
 {
     __shared__ SmemQ sq;
+    __shared__ uint64_t cnt[SLICE_GROUP];
     __shared__ uint64_t wsum[32];
     __shared__ bool last;
     load_smemq(q, sq);
@@ -370,83 +370,149 @@ __global__ void __launch_bounds__(1024, 2) k_pair_slice_runs(const __grid_consta
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
     const uint64_t S = sc.ctr[CTR_SEFF];
     const SliceSplit split = planned_split(sc.ctr);
-    const uint64_t s = (uint64_t)blockIdx.x * 32 + w;
     bool fault = false;
-    uint64_t c = 0;
-    if (s < S) {
-        const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
-        if (k1 > k0) c = slice_count_runs(q, sq.h, sq.dvh, sc.starts, s, k1 - k0, lane, hk, T3, &fault);
-    }
-    c = warp_sum_u64(c);
-    if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
-    if (lane == 0) {
-        wsum[w] = c;
-        if (s < S) sc.slice_cnt[s] = c;
-    }
-    __syncthreads();
-    if (w == 0) {  // offsets within the group, and the group's total
-        const uint64_t v = wsum[lane];
-        uint64_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t t = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += t;
-        }
-        const uint64_t sl = (uint64_t)blockIdx.x * 32 + lane;
-        if (sl < S) sc.slice_off[sl] = x - v;
-        if (lane == 31) {
-            sc.blk[blockIdx.x] = x;
-            __threadfence();  // the total is visible before the ticket
-            const unsigned long long t = atomicAdd((unsigned long long*)&sc.ctr[CTR_DONE], 1ull);
-            last = t == gridDim.x - 1;
-        }
-    }
-    __syncthreads();
-    if (!last) return;
-    // the last block: exclusive scan of the group totals (in place), the total
-    __threadfence();
-    const uint32_t nb = gridDim.x;
-    uint64_t carry = 0;
-    for (uint32_t base = 0; base < nb; base += blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        const uint64_t v = i < nb ? *(volatile uint64_t*)&sc.blk[i] : 0;
-        uint64_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t t = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += t;
-        }
-        __syncthreads();  // wsum is free
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            uint64_t y = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t t = __shfl_up_sync(FULL, y, o);
-                if (lane >= o) y += t;
+    constexpr int PER_WARP = SLICE_GROUP / 32;
+    for (int i = 0; i < PER_WARP; i++) {
+        const uint64_t s = (uint64_t)blockIdx.x * SLICE_GROUP + w * PER_WARP + i;
+        uint64_t c = 0;
+        if (s < S) {
+            const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
+            if (k1 > k0) {
+                RunPrefix rp;
+                const int32_t b = warp_load_start(q, sq.h, sc.starts, s, lane, rp);
+                c = slice_count_runs(q, sq.h, sq.dvh, rp, b, k1 - k0, lane, hk, T3, &fault);
             }
-            wsum[lane] = y;
         }
-        __syncthreads();
-        if (i < nb) sc.blk[i] = carry + (w > 0 ? wsum[w - 1] : 0) + x - v;
-        carry += wsum[31];
+        c = warp_sum_u64(c);
+        if (lane == 0) {
+            cnt[w * PER_WARP + i] = c;
+            if (s < S) sc.slice_cnt[s] = c;
+        }
     }
+    if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // the end of the last slice: row offset S = the total
-        if ((S & 31) == 0) sc.blk[S >> 5] = carry;
-        sc.slice_off[S] = carry - sc.blk[S >> 5];
-        sc.ctr[CTR_TOTAL] = carry;
-        if (dev_count) *dev_count = carry;
-    }
+    group_offsets(sc, cnt, S, dev_count, wsum, &last);
 }
 
 cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
                                    uint64_t S_req, uint64_t* dev_count, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)((S_req + 31) / 32);
+    const unsigned blocks = (unsigned)((S_req + SLICE_GROUP - 1) / SLICE_GROUP);
     k_pair_slice_runs<<<blocks, 1024, 0, st>>>(q, sc, T3, dev_count);
+    return cudaGetLastError();
+}
+
+// The planner and the run-level slice counts in one launch, with the leaf
+// counts W and the trailing-three table T3 built in each block's shared memory
+// (when both fit): every block computes the tables (O(P n), microseconds),
+// then its warps unrank their slices' starts (as k_plan) and count them run by
+// run (as k_pair_slice_runs) straight from the start they just found; the
+// grid also writes the pair tables the write walk reads.  The fastest first
+// half of fs_enumerate: one launch instead of tables, planner and counts.
+__global__ void __launch_bounds__(1024) k_plan_runs(const __grid_constant__ QueryConst q,
+                                                    Scratch sc, uint64_t S_req, int auto_s,
+                                                    uint64_t min_leaves, uint64_t* dev_count)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ uint64_t part64[1024];
+    __shared__ int32_t part32[1024];
+    __shared__ int32_t hs[FS_MAX_D];
+    __shared__ Div32 dvh[FS_MAX_D];
+    __shared__ uint64_t cnt[SLICE_GROUP];
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t sS, sL, sQ, sR;
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int len = q.n + 1;
+    uint64_t* Ws = (uint64_t*)dyn;               // nw * (n + 1)
+    uint64_t* T3 = Ws + (size_t)q.nw * len;      // n + 1
+    if (tid < FS_MAX_D) {
+        hs[tid] = q.h[tid];
+        dvh[tid] = q.dv_h[tid];
+    }
+    if (q.tab_xy)  // the write walk's pair tables, spread over the grid
+        pair_tables_fill(q, nullptr, sc.X0, sc.YD, blockIdx.x * blockDim.x + tid,
+                         gridDim.x * blockDim.x);
+    for (int k = q.P - 2; k >= 0; k--) {
+        const uint64_t* in = (k == q.P - 2) ? nullptr : Ws + (size_t)(k + 1) * len;
+        block_strided_prefix_sum(in, q.dv_in, Ws + (size_t)k * len, len, q.h[k], part64);
+    }
+    trailing_tables_block(q, 3, T3, nullptr, nullptr, part64, part32);
+    if (tid == 0) {
+        const uint64_t L = total_leaves(q, Ws);
+        uint64_t S = S_req;
+        if (auto_s) {
+            uint64_t want = (L + min_leaves - 1) / min_leaves;
+            if (want < 1) want = 1;
+            if (want < S) S = want;
+        }
+        const SliceSplit sp(L, S);
+        sS = S;
+        sL = L;
+        sQ = sp.Q;
+        sR = sp.R;
+        if (blockIdx.x == 0) {
+            sc.ctr[CTR_SEFF] = S;
+            sc.ctr[CTR_L] = L;
+            sc.ctr[CTR_SQ] = sp.Q;
+            sc.ctr[CTR_SR] = sp.R;
+        }
+    }
+    __syncthreads();
+    const uint64_t S = sS, L = sL;
+    SliceSplit split;
+    split.Q = sQ;
+    split.R = sR;
+    const int32_t hk = lane < q.P - 1 ? hs[lane] : 0;
+    bool fault = false;
+    constexpr int PER_WARP = SLICE_GROUP / 32;
+    // the warp's PER_WARP consecutive slices: unrank the first start, then each
+    // count leaves the walk at the next slice's start
+    RunPrefix rp;
+    int32_t b = 0;
+    bool have = false;
+    for (int i = 0; i < PER_WARP; i++) {
+        const uint64_t s = (uint64_t)blockIdx.x * SLICE_GROUP + w * PER_WARP + i;
+        uint64_t c = 0;
+        if (s < S) {
+            int32_t* st = sc.starts + s * START_W;
+            const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
+            if (k0 >= L) {
+                if (lane == 0) st[START_W - 1] = -1;
+            } else {
+                if (!have) {
+                    b = warp_unrank(q, hs, dvh, Ws, k0, lane, rp);
+                    have = true;
+                }
+                if (lane < q.P - 1) st[lane] = rp.a;
+                if (lane == 0) st[START_W - 1] = b;
+                c = runs_count_advance(q, hs, dvh, rp, b, k1 - k0, lane, hk, T3, &fault);
+            }
+        }
+        c = warp_sum_u64(c);
+        if (lane == 0) {
+            cnt[w * PER_WARP + i] = c;
+            if (s < S) sc.slice_cnt[s] = c;
+        }
+    }
+    if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
+    __syncthreads();
+    group_offsets(sc, cnt, S, dev_count, wsum, &last);
+}
+
+size_t plan_runs_smem_bytes(const QueryConst& q)
+{
+    return ((size_t)q.nw + 1) * (size_t)(q.n + 1) * 8;
+}
+
+cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
+                             uint64_t min_leaves, uint64_t* dev_count, cudaStream_t st)
+{
+    const size_t smem = plan_runs_smem_bytes(q);
+    cudaError_t e = smem_optin((const void*)k_plan_runs, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((S_req + SLICE_GROUP - 1) / SLICE_GROUP);
+    k_plan_runs<<<blocks, 1024, smem, st>>>(q, sc, S_req, auto_s, min_leaves, dev_count);
     return cudaGetLastError();
 }
 

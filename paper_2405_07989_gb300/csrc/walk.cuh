@@ -444,12 +444,12 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
 // Returns this lane's part of the slice count (the caller sums the warp);
 // *fault is set if the slice claims leaves past the last one.
 // ---------------------------------------------------------------------------
+// rp, b: the slice's start (run prefix in the lanes, index in the first run);
+// T3 in global or shared memory.
 FS_D uint64_t slice_count_runs(const QueryConst& q, const int32_t* hs, const Div32* dvh,
-                               const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
-                               int32_t hk, const uint64_t* T3, bool* fault)
+                               RunPrefix rp, int32_t b, uint64_t nleaves, int lane, int32_t hk,
+                               const uint64_t* T3, bool* fault)
 {
-    RunPrefix rp;
-    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
     const int np = q.P - 1;
     const int32_t hin = hs[np];
     uint64_t rem = nleaves;
@@ -480,7 +480,7 @@ FS_D uint64_t slice_count_runs(const QueryConst& q, const int32_t* hs, const Div
         if (m > 0) {
             const int32_t r0 = R - bj * hin;
             const int32_t r1 = r0 - (int32_t)m * hin;
-            acc += __ldg(&T3[r0]) - (r1 >= 0 ? __ldg(&T3[r1]) : 0ull);
+            acc += T3[r0] - (r1 >= 0 ? T3[r1] : 0ull);
         }
         const uint64_t tot = __shfl_sync(FULL, incl, 31);
         if (tot >= rem) return acc;
@@ -566,10 +566,162 @@ FS_D void publish_count(uint64_t* ctr, uint64_t* dev_count)
     }
 }
 
+// The same count, resumable: counts the nleaves leaves from (rp, b) and moves
+// (rp, b) to the leaf after them -- the start of the next slice -- so a warp
+// that counts consecutive slices unranks only the first.  When the leaves end
+// with the last run of the space, (rp, b) is left as it was (nothing follows).
+FS_D uint64_t runs_count_advance(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                                 RunPrefix& rp, int32_t& b, uint64_t nleaves, int lane, int32_t hk,
+                                 const uint64_t* T3, bool* fault)
+{
+    const int np = q.P - 1;
+    const int32_t hin = hs[np];
+    uint64_t rem = nleaves;
+    uint64_t acc = 0;
+    for (;;) {
+        int32_t Rc = q.n, ac = 0;
+        uint32_t hsib = 0, nsib = 1;
+        if (np > 0) {
+            Rc = __shfl_sync(FULL, rp.r, np - 1);
+            ac = __shfl_sync(FULL, rp.a, np - 1);
+            hsib = (uint32_t)hs[np - 1];
+            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            if (nsib > 32) nsib = 32;
+        }
+        const bool act = (uint32_t)lane < nsib;
+        const int32_t R = (int32_t)((uint32_t)Rc - (uint32_t)lane * hsib);
+        const int32_t bj = lane == 0 ? b : 0;
+        const uint64_t len = act ? (uint64_t)(div32((uint32_t)R, q.dv_in) + 1 - (uint32_t)bj) : 0;
+        uint64_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint64_t excl = incl - len;
+        const uint64_t m = excl >= rem ? 0 : (rem - excl < len ? rem - excl : len);
+        if (m > 0) {
+            const int32_t r0 = R - bj * hin;
+            const int32_t r1 = r0 - (int32_t)m * hin;
+            acc += T3[r0] - (r1 >= 0 ? T3[r1] : 0ull);
+        }
+        const uint64_t tot = __shfl_sync(FULL, incl, 31);
+        if (tot > rem) {
+            // the leaves end inside run js of the group: the next one starts there
+            const int js = __ffs(__ballot_sync(FULL, act && incl > rem)) - 1;
+            const uint64_t ex = __shfl_sync(FULL, excl, js);
+            b = (js == 0 ? b : 0) + (int32_t)(rem - ex);
+            if (np > 0 && lane == np - 1) {
+                rp.a = ac + js;
+                rp.r = (int32_t)((uint32_t)Rc - (uint32_t)js * hsib);
+            }
+            return acc;
+        }
+        if (np == 0) {
+            if (tot < rem) *fault = true;  // more leaves claimed than the space has
+            return acc;
+        }
+        // the group is used up: step past its last run
+        RunPrefix nx = rp;
+        if (lane == np - 1) {
+            nx.a = ac + (int32_t)nsib - 1;
+            nx.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
+        }
+        const bool more = warp_next_run(q, lane, hk, nx);
+        if (tot == rem) {
+            if (more) {
+                rp = nx;
+                b = 0;
+            }
+            return acc;
+        }
+        if (!more) {
+            *fault = true;
+            return acc;
+        }
+        rp = nx;
+        rem -= tot;
+        b = 0;
+    }
+}
+
 // The first output row of slice s (see Scratch::blk).
 FS_D uint64_t slice_row0(const Scratch& sc, uint64_t s)
 {
-    return sc.slice_off[s] + (sc.blk ? sc.blk[s >> 5] : 0ull);
+    return sc.slice_off[s] + (sc.blk ? sc.blk[s / SLICE_GROUP] : 0ull);
+}
+
+// Offsets of slices counted group by group (SLICE_GROUP slices per block,
+// counts in shared memory cnt[]): writes each slice's offset within its group
+// to slice_off and the group total to blk[blockIdx.x]; the last block to
+// finish (ticket in ctr[CTR_DONE]) turns blk into exclusive group offsets and
+// writes the total to ctr[CTR_TOTAL] and *dev_count.  Called by every thread
+// of a 1024-thread block; wsum: 32 shared words; last: a shared flag.
+FS_D void group_offsets(const Scratch& sc, const uint64_t* cnt, uint64_t S, uint64_t* dev_count,
+                        uint64_t* wsum, bool* last)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t g0 = (uint64_t)blockIdx.x * SLICE_GROUP;
+    uint64_t v = tid < SLICE_GROUP ? cnt[tid] : 0, x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (tid < SLICE_GROUP) {
+        uint64_t before = 0;
+        for (int k = 0; k < w; k++) before += wsum[k];
+        if (g0 + tid < S) sc.slice_off[g0 + tid] = before + x - v;
+    }
+    if (tid == 0) {
+        uint64_t tot = 0;
+        for (int k = 0; k < SLICE_GROUP / 32; k++) tot += wsum[k];
+        sc.blk[blockIdx.x] = tot;
+        __threadfence();  // the total is visible before the ticket
+        const unsigned long long t = atomicAdd((unsigned long long*)&sc.ctr[CTR_DONE], 1ull);
+        *last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!*last) return;
+    // the last block: exclusive scan of the group totals (in place), the total
+    __threadfence();
+    const uint32_t nb = gridDim.x;
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + tid;
+        const uint64_t y0 = i < nb ? *(volatile uint64_t*)&sc.blk[i] : 0;
+        uint64_t y = y0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += t;
+        }
+        __syncthreads();  // wsum is free
+        if (lane == 31) wsum[w] = y;
+        __syncthreads();
+        if (w == 0) {
+            uint64_t z = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(FULL, z, o);
+                if (lane >= o) z += t;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        if (i < nb) sc.blk[i] = carry + (w > 0 ? wsum[w - 1] : 0) + y - y0;
+        carry += wsum[31];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // the end of the last slice: row offset S = the total
+        if (S % SLICE_GROUP == 0) sc.blk[S / SLICE_GROUP] = carry;
+        sc.slice_off[S] = carry - sc.blk[S / SLICE_GROUP];
+        sc.ctr[CTR_TOTAL] = carry;
+        if (dev_count) *dev_count = carry;
+    }
 }
 
 // Sets the device error flag the host checks after a synchronous call.
