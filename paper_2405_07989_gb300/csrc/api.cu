@@ -333,8 +333,9 @@ fs_config cfg_or_default(const fs_config* cfg)
 // Enumerate counts its slices run by run from the trailing-three table (n + 1
 // uint64 entries) below this n, leaf by leaf above it.
 constexpr int32_t RUNS_MAX_N = 1 << 20;
-// ... and builds that table and the leaf counts in each planner block's shared
-// memory (one launch for tables, planner and counts) while they fit in this.
+// ... and, while the leaf counts and the prefix-count tables fit in this much
+// shared memory, builds them in each planner block and takes every slice's
+// offset from them (one launch for tables, planner and offsets).
 constexpr size_t PLAN_RUNS_SMEM_MAX = 200 * 1024;
 
 // Trailing levels the tables can take for q under `method` (0: none).
@@ -498,7 +499,7 @@ struct Call {
     int method = FS_METHOD_PAIR;  // PLAIN, PAIR, or TRIPLE for the trailing-k tables
     int trail = 0;                // TRIPLE: k = 3 or 4 trailing levels in the tables
     bool runs = false;            // PAIR enumerate: per-slice counts run by run from T3
-    bool fused = false;           // runs, with tables, planner and counts in one launch
+    bool fused = false;           // tables, planner and offsets (prefix counts) in one launch
     Op op = OP_COUNT;
     DevState* ds = nullptr;
     Scratch sc;
@@ -568,7 +569,7 @@ fs_status prepare_device(Call& c, void* base)
     const QueryConst& qw = c.wq();
     const Op op = c.op;
     c.sc = scratch_at(base, c.L);
-    if (c.runs) c.sc.blk = (uint64_t*)((char*)base + c.L.blk);
+    if (c.runs && !c.fused) c.sc.blk = (uint64_t*)((char*)base + c.L.blk);
     if (triple || c.runs) {
         char* b = (char*)base;
         c.T3 = (uint64_t*)(b + c.L.T3);

@@ -107,7 +107,7 @@ struct QueryConst {
 // ---------------------------------------------------------------------------
 // Slices counted per block when enumerate's first walk goes run by run (the
 // groups of Scratch::blk).
-constexpr int SLICE_GROUP = 256;
+constexpr int SLICE_GROUP = 32;
 
 enum Ctr {
     CTR_QUEUE = 0,    // slice queue head (first walk)

@@ -50,8 +50,9 @@ cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
 // Enumerate's first walk, run by run (k_pair_slice_runs): per-slice counts,
 // the two-level offsets of Scratch::blk, the total (ctr[CTR_TOTAL] and, if
 // not NULL, *dev_count).  S_req: the planner's maximum slice count.
-// The planner and enumerate's run-level counts in one launch, the tables in
-// shared memory (k_plan_runs); usable when plan_runs_smem_bytes(q) fits.
+// The planner and enumerate's slice offsets in one launch, from prefix-count
+// tables in shared memory (k_plan_offsets); usable when plan_runs_smem_bytes(q)
+// fits.  Offsets are global (Scratch::blk unused).
 size_t plan_runs_smem_bytes(const QueryConst& q);
 cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
                              uint64_t min_leaves, uint64_t* dev_count, cudaStream_t st);

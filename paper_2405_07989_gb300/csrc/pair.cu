@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(1024) k_pair_slice_runs(const __grid_constant_
     }
     if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
     __syncthreads();
-    group_offsets(sc, cnt, S, dev_count, wsum, &last);
+    group_offsets(sc, cnt, blockIdx.x, gridDim.x, S, dev_count, wsum, &last);
 }
 
 cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const uint64_t* T3,
@@ -402,30 +402,34 @@ cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const
     return cudaGetLastError();
 }
 
-// The planner and the run-level slice counts in one launch, with the leaf
-// counts W and the trailing-three table T3 built in each block's shared memory
-// (when both fit): every block computes the tables (O(P n), microseconds),
-// then its warps unrank their slices' starts (as k_plan) and count them run by
-// run (as k_pair_slice_runs) straight from the start they just found; the
-// grid also writes the pair tables the write walk reads.  The fastest first
-// half of fs_enumerate: one launch instead of tables, planner and counts.
-__global__ void __launch_bounds__(1024) k_plan_runs(const __grid_constant__ QueryConst q,
-                                                    Scratch sc, uint64_t S_req, int auto_s,
-                                                    uint64_t min_leaves, uint64_t* dev_count)
+// The planner and enumerate's slice offsets in one launch, with no walk: the
+// factorizations before a lex position are a sum of prefix counts.  With
+// C_{P-1} = T3 (the trailing-three table) and C_k[p] = sum_{x >= 0}
+// C_{k+1}[p - x h_k] (the trailing tables carried up to level k: the
+// factorizations of p over levels k..D-1), the rows before the position with
+// prefix (a_0..a_{P-2}), run index b = a_{P-1} and residuals p_0 = n,
+// p_{k+1} = p_k - a_k h_k number
+//   F = sum_{k <= P-1} (C_k[p_k] - C_k[p_k - a_k h_k]),
+// each term the factorizations whose level-k coordinate is below a_k.  Every
+// block builds W (leaf counts, for unranking) and C in shared memory (when
+// they fit), then its warps unrank slice starts (as k_plan) and write
+// slice_off[s] = F(start of s) directly; the total is C_0[n].  The grid also
+// writes the pair tables the write walk reads.
+__global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ QueryConst q,
+                                                       Scratch sc, uint64_t S_req, int auto_s,
+                                                       uint64_t min_leaves, uint64_t* dev_count)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint64_t part64[1024];
     __shared__ int32_t part32[1024];
     __shared__ int32_t hs[FS_MAX_D];
     __shared__ Div32 dvh[FS_MAX_D];
-    __shared__ uint64_t cnt[SLICE_GROUP];
-    __shared__ uint64_t wsum[32];
     __shared__ uint64_t sS, sL, sQ, sR;
-    __shared__ bool last;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int len = q.n + 1;
-    uint64_t* Ws = (uint64_t*)dyn;               // nw * (n + 1)
-    uint64_t* T3 = Ws + (size_t)q.nw * len;      // n + 1
+    const int P = q.P;
+    uint64_t* Ws = (uint64_t*)dyn;               // (P-1) x (n+1) leaf counts
+    uint64_t* C = Ws + (size_t)q.nw * len;       // P x (n+1) prefix counts
     if (tid < FS_MAX_D) {
         hs[tid] = q.h[tid];
         dvh[tid] = q.dv_h[tid];
@@ -433,11 +437,14 @@ __global__ void __launch_bounds__(1024) k_plan_runs(const __grid_constant__ Quer
     if (q.tab_xy)  // the write walk's pair tables, spread over the grid
         pair_tables_fill(q, nullptr, sc.X0, sc.YD, blockIdx.x * blockDim.x + tid,
                          gridDim.x * blockDim.x);
-    for (int k = q.P - 2; k >= 0; k--) {
-        const uint64_t* in = (k == q.P - 2) ? nullptr : Ws + (size_t)(k + 1) * len;
+    for (int k = P - 2; k >= 0; k--) {
+        const uint64_t* in = (k == P - 2) ? nullptr : Ws + (size_t)(k + 1) * len;
         block_strided_prefix_sum(in, q.dv_in, Ws + (size_t)k * len, len, q.h[k], part64);
     }
-    trailing_tables_block(q, 3, T3, nullptr, nullptr, part64, part32);
+    trailing_tables_block(q, 3, C + (size_t)(P - 1) * len, nullptr, nullptr, part64, part32);
+    for (int k = P - 2; k >= 0; k--)
+        block_strided_prefix_sum(C + (size_t)(k + 1) * len, q.dv_in, C + (size_t)k * len, len,
+                                 q.h[k], part64);
     if (tid == 0) {
         const uint64_t L = total_leaves(q, Ws);
         uint64_t S = S_req;
@@ -456,6 +463,10 @@ __global__ void __launch_bounds__(1024) k_plan_runs(const __grid_constant__ Quer
             sc.ctr[CTR_L] = L;
             sc.ctr[CTR_SQ] = sp.Q;
             sc.ctr[CTR_SR] = sp.R;
+            const uint64_t total = C[q.n];  // C_0[n] = |Z|
+            sc.ctr[CTR_TOTAL] = total;
+            sc.slice_off[S] = total;
+            if (dev_count) *dev_count = total;
         }
     }
     __syncthreads();
@@ -463,56 +474,58 @@ __global__ void __launch_bounds__(1024) k_plan_runs(const __grid_constant__ Quer
     SliceSplit split;
     split.Q = sQ;
     split.R = sR;
-    const int32_t hk = lane < q.P - 1 ? hs[lane] : 0;
-    bool fault = false;
-    constexpr int PER_WARP = SLICE_GROUP / 32;
-    // the warp's PER_WARP consecutive slices: unrank the first start, then each
-    // count leaves the walk at the next slice's start
-    RunPrefix rp;
-    int32_t b = 0;
-    bool have = false;
-    for (int i = 0; i < PER_WARP; i++) {
-        const uint64_t s = (uint64_t)blockIdx.x * SLICE_GROUP + w * PER_WARP + i;
-        uint64_t c = 0;
-        if (s < S) {
-            int32_t* st = sc.starts + s * START_W;
-            const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
-            if (k0 >= L) {
-                if (lane == 0) st[START_W - 1] = -1;
-            } else {
-                if (!have) {
-                    b = warp_unrank(q, hs, dvh, Ws, k0, lane, rp);
-                    have = true;
-                }
-                if (lane < q.P - 1) st[lane] = rp.a;
-                if (lane == 0) st[START_W - 1] = b;
-                c = runs_count_advance(q, hs, dvh, rp, b, k1 - k0, lane, hk, T3, &fault);
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + tid) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t s = gw; s < S; s += nw) {
+        int32_t* st = sc.starts + s * START_W;
+        const uint64_t k0 = split.start(s);
+        if (k0 >= L) {  // empty slice: starts at the end
+            if (lane == 0) {
+                st[START_W - 1] = -1;
+                sc.slice_off[s] = C[q.n];
             }
+            continue;
         }
-        c = warp_sum_u64(c);
-        if (lane == 0) {
-            cnt[w * PER_WARP + i] = c;
-            if (s < S) sc.slice_cnt[s] = c;
+        RunPrefix rp;
+        const int32_t b = warp_unrank(q, hs, dvh, Ws, k0, lane, rp);
+        if (lane < P - 1) st[lane] = rp.a;
+        if (lane == 0) st[START_W - 1] = b;
+        // lane k < P-1 holds level k: a = rp.a, residual after it rp.r; before
+        // it, lane k-1's residual (n for level 0); level P-1 is (b, its run)
+        const int32_t after = rp.r;
+        int32_t before = __shfl_up_sync(FULL, after, 1);
+        if (lane == 0) before = q.n;
+        uint64_t f = 0;
+        if (lane < P - 1) {
+            const uint64_t* Ck = C + (size_t)lane * len;
+            f = Ck[before] - Ck[after];
+        } else if (lane == P - 1) {
+            const uint64_t* Ck = C + (size_t)(P - 1) * len;
+            const int32_t pr = P >= 2 ? before : q.n;  // the run's residual
+            f = Ck[pr] - Ck[pr - b * hs[P - 1]];
         }
+        f = warp_sum_u64(f);
+        if (lane == 0) sc.slice_off[s] = f;
     }
-    if (__any_sync(FULL, fault)) flag_fault(sc.ctr);
-    __syncthreads();
-    group_offsets(sc, cnt, S, dev_count, wsum, &last);
 }
 
 size_t plan_runs_smem_bytes(const QueryConst& q)
 {
-    return ((size_t)q.nw + 1) * (size_t)(q.n + 1) * 8;
+    return ((size_t)q.nw + (size_t)q.P) * (size_t)(q.n + 1) * 8;
 }
 
 cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_req, int auto_s,
                              uint64_t min_leaves, uint64_t* dev_count, cudaStream_t st)
 {
     const size_t smem = plan_runs_smem_bytes(q);
-    cudaError_t e = smem_optin((const void*)k_plan_runs, (int)smem);
+    cudaError_t e = smem_optin((const void*)k_plan_offsets, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((S_req + SLICE_GROUP - 1) / SLICE_GROUP);
-    k_plan_runs<<<blocks, 1024, smem, st>>>(q, sc, S_req, auto_s, min_leaves, dev_count);
+    int sms = 0;
+    e = sm_count_cached(&sms);
+    if (e != cudaSuccess) return e;
+    const uint64_t need = (S_req + 31) / 32;  // 32 warps per block
+    const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
+    k_plan_offsets<<<blocks, 1024, smem, st>>>(q, sc, S_req, auto_s, min_leaves, dev_count);
     return cudaGetLastError();
 }
 

@@ -566,102 +566,24 @@ FS_D void publish_count(uint64_t* ctr, uint64_t* dev_count)
     }
 }
 
-// The same count, resumable: counts the nleaves leaves from (rp, b) and moves
-// (rp, b) to the leaf after them -- the start of the next slice -- so a warp
-// that counts consecutive slices unranks only the first.  When the leaves end
-// with the last run of the space, (rp, b) is left as it was (nothing follows).
-FS_D uint64_t runs_count_advance(const QueryConst& q, const int32_t* hs, const Div32* dvh,
-                                 RunPrefix& rp, int32_t& b, uint64_t nleaves, int lane, int32_t hk,
-                                 const uint64_t* T3, bool* fault)
-{
-    const int np = q.P - 1;
-    const int32_t hin = hs[np];
-    uint64_t rem = nleaves;
-    uint64_t acc = 0;
-    for (;;) {
-        int32_t Rc = q.n, ac = 0;
-        uint32_t hsib = 0, nsib = 1;
-        if (np > 0) {
-            Rc = __shfl_sync(FULL, rp.r, np - 1);
-            ac = __shfl_sync(FULL, rp.a, np - 1);
-            hsib = (uint32_t)hs[np - 1];
-            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
-            if (nsib > 32) nsib = 32;
-        }
-        const bool act = (uint32_t)lane < nsib;
-        const int32_t R = (int32_t)((uint32_t)Rc - (uint32_t)lane * hsib);
-        const int32_t bj = lane == 0 ? b : 0;
-        const uint64_t len = act ? (uint64_t)(div32((uint32_t)R, q.dv_in) + 1 - (uint32_t)bj) : 0;
-        uint64_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint64_t excl = incl - len;
-        const uint64_t m = excl >= rem ? 0 : (rem - excl < len ? rem - excl : len);
-        if (m > 0) {
-            const int32_t r0 = R - bj * hin;
-            const int32_t r1 = r0 - (int32_t)m * hin;
-            acc += T3[r0] - (r1 >= 0 ? T3[r1] : 0ull);
-        }
-        const uint64_t tot = __shfl_sync(FULL, incl, 31);
-        if (tot > rem) {
-            // the leaves end inside run js of the group: the next one starts there
-            const int js = __ffs(__ballot_sync(FULL, act && incl > rem)) - 1;
-            const uint64_t ex = __shfl_sync(FULL, excl, js);
-            b = (js == 0 ? b : 0) + (int32_t)(rem - ex);
-            if (np > 0 && lane == np - 1) {
-                rp.a = ac + js;
-                rp.r = (int32_t)((uint32_t)Rc - (uint32_t)js * hsib);
-            }
-            return acc;
-        }
-        if (np == 0) {
-            if (tot < rem) *fault = true;  // more leaves claimed than the space has
-            return acc;
-        }
-        // the group is used up: step past its last run
-        RunPrefix nx = rp;
-        if (lane == np - 1) {
-            nx.a = ac + (int32_t)nsib - 1;
-            nx.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
-        }
-        const bool more = warp_next_run(q, lane, hk, nx);
-        if (tot == rem) {
-            if (more) {
-                rp = nx;
-                b = 0;
-            }
-            return acc;
-        }
-        if (!more) {
-            *fault = true;
-            return acc;
-        }
-        rp = nx;
-        rem -= tot;
-        b = 0;
-    }
-}
-
 // The first output row of slice s (see Scratch::blk).
 FS_D uint64_t slice_row0(const Scratch& sc, uint64_t s)
 {
     return sc.slice_off[s] + (sc.blk ? sc.blk[s / SLICE_GROUP] : 0ull);
 }
 
-// Offsets of slices counted group by group (SLICE_GROUP slices per block,
-// counts in shared memory cnt[]): writes each slice's offset within its group
-// to slice_off and the group total to blk[blockIdx.x]; the last block to
-// finish (ticket in ctr[CTR_DONE]) turns blk into exclusive group offsets and
-// writes the total to ctr[CTR_TOTAL] and *dev_count.  Called by every thread
-// of a 1024-thread block; wsum: 32 shared words; last: a shared flag.
-FS_D void group_offsets(const Scratch& sc, const uint64_t* cnt, uint64_t S, uint64_t* dev_count,
-                        uint64_t* wsum, bool* last)
+// Offsets of slices counted group by group (SLICE_GROUP slices, counts in
+// shared memory cnt[]): writes each slice of group grp its offset within the
+// group (slice_off) and the group total (blk[grp]); the block that finishes
+// the last of the ngroups groups (ticket in ctr[CTR_DONE]) turns blk into
+// exclusive group offsets and writes the total to ctr[CTR_TOTAL] and
+// *dev_count.  Called by every thread of a 1024-thread block; wsum: 32 shared
+// words; last: a shared flag.
+FS_D void group_offsets(const Scratch& sc, const uint64_t* cnt, uint64_t grp, uint32_t ngroups,
+                        uint64_t S, uint64_t* dev_count, uint64_t* wsum, bool* last)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint64_t g0 = (uint64_t)blockIdx.x * SLICE_GROUP;
+    const uint64_t g0 = grp * SLICE_GROUP;
     uint64_t v = tid < SLICE_GROUP ? cnt[tid] : 0, x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -678,16 +600,16 @@ FS_D void group_offsets(const Scratch& sc, const uint64_t* cnt, uint64_t S, uint
     if (tid == 0) {
         uint64_t tot = 0;
         for (int k = 0; k < SLICE_GROUP / 32; k++) tot += wsum[k];
-        sc.blk[blockIdx.x] = tot;
+        sc.blk[grp] = tot;
         __threadfence();  // the total is visible before the ticket
         const unsigned long long t = atomicAdd((unsigned long long*)&sc.ctr[CTR_DONE], 1ull);
-        *last = t == gridDim.x - 1;
+        *last = t == ngroups - 1;
     }
     __syncthreads();
     if (!*last) return;
-    // the last block: exclusive scan of the group totals (in place), the total
+    // the last group: exclusive scan of the group totals (in place), the total
     __threadfence();
-    const uint32_t nb = gridDim.x;
+    const uint32_t nb = ngroups;
     uint64_t carry = 0;
     for (uint32_t base = 0; base < nb; base += blockDim.x) {
         const uint32_t i = base + tid;
