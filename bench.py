@@ -384,6 +384,8 @@ def run_gpu(args):
         extras = heavy_count_extras(fs, workloads, dev)
         extras["batched"] = batch_extras(fs, workloads, dev)
         extras["serving"] = serving_extras(fs, workloads, args.serve_rate, args.serve_requests)
+        # capacity: the same requests all at once (no arrival pacing)
+        extras["serving_saturated"] = serving_extras(fs, workloads, 1e9, args.serve_requests)
         extras["table1_context"] = table1_extras(fs, dev)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----

@@ -64,11 +64,49 @@ FS_D uint64_t sps_in(const uint64_t* in, int p, const Div32& dv_in)
     return in ? in[p] : (uint64_t)div32((uint32_t)p, dv_in) + 1;
 }
 
+// Few, short chains (a small table): one warp per chain, 32 consecutive chain
+// elements per step with a warp scan -- no block-wide barriers, which is what
+// the segmented form below spends its time on at this size.
+FS_D bool strided_by_warps(int len, int s)
+{
+    return s <= 2 * (int)(blockDim.x >> 5) && (len - 1) / s + 1 <= 256;
+}
+
+template <class T, class Op, class In>
+FS_D void warp_chains_scan(In in, T* out, int len, int s, Op op, T ident)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rho = threadIdx.x >> 5; rho < s; rho += nw) {
+        T carry = ident;
+        for (int t0 = 0;; t0 += 32) {
+            const long long p = rho + (long long)(t0 + lane) * s;
+            if (!__any_sync(FULL, p < len)) break;
+            T x = p < len ? in((int)p) : ident;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x = op(y, x);
+            }
+            if (p < len) out[p] = op(carry, x);
+            carry = op(carry, __shfl_sync(FULL, x, 31));
+        }
+    }
+    __syncthreads();
+}
+
 FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint64_t* out, int len,
                                    int s, uint64_t* part)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     if (len <= 0) return;
+    if (s < len && strided_by_warps(len, s)) {
+        struct Add {
+            FS_D uint64_t operator()(uint64_t a, uint64_t b) const { return a + b; }
+        };
+        warp_chains_scan<uint64_t>([&](int p) { return sps_in(in, p, dv_in); }, out, len, s, Add(),
+                                   (uint64_t)0);
+        return;
+    }
     if (s >= T || s >= len) {
         // many short chains: one thread per chain
         int nch = s < len ? s : len;
@@ -139,6 +177,10 @@ FS_D void block_strided_scan(T* x, int len, int s, T* part, T ident, Op op)
 {
     const int NT = blockDim.x, tid = threadIdx.x;
     if (len <= 0) return;
+    if (s < len && strided_by_warps(len, s)) {
+        warp_chains_scan<T>([&](int p) { return x[p]; }, x, len, s, op, ident);
+        return;
+    }
     if (s >= NT || s >= len) {
         const int nch = s < len ? s : len;
         for (int rho = tid; rho < nch; rho += NT) {
