@@ -148,3 +148,53 @@ def test_server_enumerate_waits_for_release():
         srv.release(b)
         with pytest.raises(fs.FsError):
             srv.release(b)
+
+
+def test_server_serving_workload_full():
+    """The serving workload at its full size: 2000 requests drawn like the
+    batched ones with n up to 20000 (80 % count, 15 % lengths, 5 % enumerate),
+    all submitted at once.  Every count and length range equals the oracle's
+    DP; every admitted enumeration's rows sum to n, are strictly increasing in
+    the walk order (descending generators) and number |Z|; enumerations larger
+    than the 32 GB budget are refused with their exact count."""
+    budget = 32 << 30
+    reqs = workloads.config5(0, 2000, 1000.0, 20000)
+    with fs.Server(mem_budget_bytes=budget, table_bytes=1 << 30, max_batch=512) as srv:
+        tickets = {srv.submit(op, n, g, elem_bytes=2): (op, n, g) for (_, op, n, g) in reqs}
+        got = {}
+        t0 = time.time()
+        rng = np.random.default_rng(1)
+        while len(got) < len(tickets):
+            for r in srv.poll(256, wait_ms=50):
+                t = r["ticket"]
+                got[t] = r
+                op, n, g = tickets[t]
+                if op == fs.REQ_ENUMERATE and r["status"] == fs.FS_OK:
+                    c, d = r["count"], len(g)
+                    if c:
+                        # the rows of a random window, checked on the device
+                        k = int(min(c, 1 << 20))
+                        lo = int(rng.integers(0, c - k + 1))
+                        rows = torch.as_tensor(_DevRows(r["rows"] + lo * d * 2, k, d, 2),
+                                               device="cuda").to(torch.int64)
+                        gv = torch.tensor(g, dtype=torch.int64, device="cuda")
+                        assert bool(((rows * gv).sum(1) == n).all()), (n, g)
+                        order = sorted(range(d), key=lambda i: -g[i])
+                        key = rows[:, order]
+                        if k > 1:
+                            diff = key[1:] - key[:-1]
+                            first = (diff != 0).to(torch.int64).argmax(1)
+                            lead = diff.gather(1, first[:, None])[:, 0]
+                            assert bool((lead > 0).all()), (n, g)
+                    srv.release(t)
+            assert time.time() - t0 < 600, f"{len(got)} of {len(tickets)} responses"
+    for t, (op, n, g) in tickets.items():
+        r = got[t]
+        c = oracle.count_dp(n, g)
+        assert r["count"] == c, (op, n, g)
+        if op == fs.REQ_ENUMERATE and c * len(g) * 2 > budget:
+            assert r["status"] == fs.FS_E_CAPACITY
+            continue
+        assert r["status"] == fs.FS_OK, (op, n, g, r["status"])
+        if op in (fs.REQ_LENGTHS, fs.REQ_ENUMERATE) and c > 0:
+            assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(n, g), (op, n, g)
