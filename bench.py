@@ -387,6 +387,7 @@ def run_gpu(args):
         # capacity: the same requests all at once (no arrival pacing)
         extras["serving_saturated"] = serving_extras(fs, workloads, 1e9, args.serve_requests)
         extras["table1_context"] = table1_extras(fs, dev)
+        extras["methods"] = method_extras(fs, workloads, dev)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----
     cpu = None
@@ -516,6 +517,51 @@ def table1_extras(fs, dev):
                     "paper_seconds_rtx3080": paper_s})
         del buf
     return out
+
+
+def method_extras(fs, workloads, dev):
+    """The single large query through the other walks, event-timed on the
+    device: the paper's Algorithm 3.1 step by step (PLAIN) for count and
+    enumerate, the PAIR count, and the predicate consumer (fs_any) with a
+    predicate no factorization satisfies (a full walk) and one the first
+    leaves satisfy (early exit)."""
+    import torch
+    n, g = workloads.CONFIG2
+    d = len(g)
+    Z = fs.fs_count(n, g)
+    out = torch.empty(Z * d, dtype=torch.int32, device=dev)
+    dc = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plain = fs.make_config(method=fs.METHOD_PLAIN)
+    pair = fs.make_config(method=fs.METHOD_PAIR)
+    res = {"workload": f"g={tuple(g)}, n={n}: {Z} factorizations"}
+    res["plain_count_ms"] = timed(lambda: fs.fs_count_async(n, g, dc, plain))
+    assert int(dc[0]) == Z
+    res["plain_enumerate_ms"] = timed(lambda: fs.fs_enumerate_async(n, g, out, Z, dc, cfg=plain), 2)
+    assert int(dc[0]) == Z
+    res["pair_count_ms"] = timed(lambda: fs.fs_count_async(n, g, dc, pair))
+    assert int(dc[0]) == Z
+    res["quad_count_ms"] = timed(lambda: fs.fs_count_async(n, g, dc))
+    # sum of a_i = -1 never holds: every leaf is visited
+    t0 = time.perf_counter()
+    assert not fs.fs_any(n, g, [1] * d, -1)
+    res["any_false_ms"] = (time.perf_counter() - t0) * 1000.0
+    t0 = time.perf_counter()
+    assert fs.fs_any(n, g, [0] * d, 0)
+    res["any_true_ms"] = (time.perf_counter() - t0) * 1000.0
+    res["plain_enumerate_factorizations_per_s"] = Z / (res["plain_enumerate_ms"] / 1000.0)
+    return res
 
 
 def batch_extras(fs, workloads, dev):
