@@ -371,10 +371,11 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
         lc.threads = 128;
         e = plain_occupancy(q, op, lc.threads, &bps);
     } else if (method == FS_METHOD_TRIPLE) {
-        int t = cfg.block_threads > 0 ? cfg.block_threads : 256;
-        if (t % 32 != 0 || t > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", t);
+        const int tdef = triple_threads(q, op);
+        int t = cfg.block_threads > 0 ? cfg.block_threads : tdef;
+        if (t % 32 != 0 || t > tdef) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= %d", t, tdef);
         lc.threads = t;
-        e = triple_occupancy(lc.threads, &bps);
+        e = triple_occupancy(q, op, lc.threads, &bps);
     } else {
         int t = cfg.block_threads > 0 ? cfg.block_threads : 256;
         if (t % 32 != 0 || t > 256) return fail(FS_E_INVAL, "block_threads %d: need a multiple of 32, <= 256", t);

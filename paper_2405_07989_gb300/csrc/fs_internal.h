@@ -123,6 +123,7 @@ enum Ctr {
     CTR_DONE = 10,    // blocks of a count walk that have added their part
     CTR_SQ = 11,      // leaves per slice, floor(L / S) (planner)
     CTR_SR = 12,      // L mod S: the first R slices have one leaf more (planner)
+    CTR_TMAX = 13,    // largest entry of the trailing count table (precompute)
     CTR_N = 16
 };
 

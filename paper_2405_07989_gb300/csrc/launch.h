@@ -46,7 +46,9 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
 
 // pair.cu: the TRIPLE walk over the reduced query q3 (OP_COUNT, OP_SLICES,
 // OP_LEN = count + min / max length)
-cudaError_t triple_occupancy(int threads, int* blocks_per_sm);
+// The trailing-table walk: its block size for q3 / op, and blocks per SM.
+int triple_threads(const QueryConst& q3, Op op);
+cudaError_t triple_occupancy(const QueryConst& q3, Op op, int threads, int* blocks_per_sm);
 // Enumerate's first walk, run by run (k_pair_slice_runs): per-slice counts,
 // the two-level offsets of Scratch::blk, the total (ctr[CTR_TOTAL] and, if
 // not NULL, *dev_count).  S_req: the planner's maximum slice count.

@@ -269,9 +269,10 @@ __global__ void __launch_bounds__(256) k_pair_any(const __grid_constant__ QueryC
 // The walk runs over the prefixes of the first D-3 levels (the reduced query
 // q3 has one prefix level fewer); the leaf with residual r contributes
 // T3[r] factorizations with lengths lp + a + [MN3[r], MX3[r]].
-template <int MODE, bool PER_SLICE>
+template <int MODE, bool PER_SLICE, bool SMEMT>
 struct TripleCons {
     const uint64_t* T3;
+    const uint32_t* T32;  // SMEMT: shared-memory uint32 copy of T3, or NULL
     const int32_t* MN3;
     const int32_t* MX3;
     uint64_t* slice_cnt;
@@ -295,7 +296,11 @@ struct TripleCons {
     FS_D bool chunk(const QueryConst&, int, bool valid, int32_t r, int32_t a, int32_t lp)
     {
         if (valid) {
-            const uint64_t c = __ldg(&T3[r]);
+            uint64_t c;
+            if constexpr (SMEMT)
+                c = T32 ? (uint64_t)T32[r] : __ldg(&T3[r]);
+            else
+                c = __ldg(&T3[r]);
             acc += c;
             if (MODE && c) {
                 mn = min(mn, lp + a + __ldg(&MN3[r]));
@@ -306,23 +311,39 @@ struct TripleCons {
     }
 };
 
-template <int MODE, bool PER_SLICE>
-__global__ void __launch_bounds__(256) k_triple_walk(const __grid_constant__ QueryConst q3,
-                                                     Scratch sc, int queue, const uint64_t* T3,
-                                                     const int32_t* MN3, const int32_t* MX3,
-                                                     uint64_t* dev_count)
+// SMEMT: the count table is copied to shared memory as uint32 (when its
+// largest entry, recorded by the precompute, fits), so the lookups of the walk
+// hit shared memory instead of L2.
+template <int MODE, bool PER_SLICE, bool SMEMT>
+__global__ void __launch_bounds__(SMEMT ? 1024 : 256) k_triple_walk(
+    const __grid_constant__ QueryConst q3, Scratch sc, int queue, const uint64_t* T3,
+    const int32_t* MN3, const int32_t* MX3, uint64_t* dev_count)
 {
     __shared__ SmemQ sq;
     __shared__ unsigned long long bsum;
     __shared__ int bmin, bmax;
+    extern __shared__ __align__(16) unsigned char dyn[];
     load_smemq(q3, sq);
     if (threadIdx.x == 0) {
         bsum = 0;
         bmin = 0x7fffffff;
         bmax = -1;
     }
+    uint32_t* T32 = nullptr;
+    if (SMEMT && sc.ctr[CTR_TMAX] <= 0xffffffffull) {
+        T32 = (uint32_t*)dyn;
+        const uint32_t len = (uint32_t)q3.n + 1, bd = blockDim.x;
+        for (uint32_t p = threadIdx.x; p < len; p += 4 * bd) {  // four loads in flight
+            uint64_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = p + k * bd < len ? __ldg(&T3[p + k * bd]) : 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (p + k * bd < len) T32[p + k * bd] = (uint32_t)v[k];
+        }
+    }
     __syncthreads();
-    TripleCons<MODE, PER_SLICE> cons{T3, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
+    TripleCons<MODE, PER_SLICE, SMEMT> cons{T3, T32, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
     run_queue(q3, sq, sc, queue, cons);
     const uint64_t v = warp_sum_u64(cons.total);
     int mn = cons.mn, mx = cons.mx;
@@ -529,9 +550,27 @@ cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_
     return cudaGetLastError();
 }
 
-cudaError_t triple_occupancy(int threads, int* nb)
+// The count modes keep a uint32 copy of the table in shared memory up to
+// this size; above it (or for the length range) the walk reads the uint64
+// table through L2.
+constexpr int TRIPLE_SMEM_MAX = 160 * 1024;
+
+static int triple_smem(const QueryConst& q3, Op op)
 {
-    return occupancy_cached((const void*)k_triple_walk<1, false>, threads, 0, nb);
+    const long long b = ((long long)q3.n + 1) * 4;
+    return (op != OP_LEN && b <= TRIPLE_SMEM_MAX) ? (int)b : 0;
+}
+
+int triple_threads(const QueryConst& q3, Op op)
+{
+    return triple_smem(q3, op) > 48 * 1024 ? 1024 : 256;  // big table: one wide block per SM
+}
+
+cudaError_t triple_occupancy(const QueryConst& q3, Op op, int threads, int* nb)
+{
+    const int smem = triple_smem(q3, op);
+    if (smem) return occupancy_cached((const void*)k_triple_walk<0, false, true>, threads, smem, nb);
+    return occupancy_cached((const void*)k_triple_walk<1, false, false>, threads, 0, nb);
 }
 
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
@@ -539,12 +578,31 @@ cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const 
                           uint64_t* dev_count, cudaStream_t st)
 {
     const dim3 g(lc.blocks), b(lc.threads);
+    const int smem = triple_smem(q3, op);
+    cudaError_t e = cudaSuccess;
     switch (op) {
-    case OP_COUNT: k_triple_walk<0, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count); break;
-    case OP_SLICES: k_triple_walk<0, true><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
-    case OP_LEN: k_triple_walk<1, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
+    case OP_COUNT:
+        if (smem) {
+            e = smem_optin((const void*)k_triple_walk<0, false, true>, smem);
+            if (e == cudaSuccess)
+                k_triple_walk<0, false, true><<<g, b, smem, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count);
+        } else {
+            k_triple_walk<0, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count);
+        }
+        break;
+    case OP_SLICES:
+        if (smem) {
+            e = smem_optin((const void*)k_triple_walk<0, true, true>, smem);
+            if (e == cudaSuccess)
+                k_triple_walk<0, true, true><<<g, b, smem, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
+        } else {
+            k_triple_walk<0, true, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
+        }
+        break;
+    case OP_LEN: k_triple_walk<1, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

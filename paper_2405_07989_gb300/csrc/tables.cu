@@ -44,6 +44,7 @@ struct PrecompArgs {
     uint64_t* T;
     int32_t* MN;
     int32_t* MX;
+    uint64_t* tmax;  // the trailing table's largest entry (ctr[CTR_TMAX])
     int32_t trail_k;
     int32_t nroles;
     int32_t role[4];
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(1024) k_precompute(const __grid_constant__ Pre
         pair_tables_fill(a.qw, a.E, a.X0, a.YD, threadIdx.x, blockDim.x);
         break;
     case ROLE_TRAIL:
-        trailing_tables_block(a.qt, a.trail_k, a.T, a.MN, a.MX, part64, part32);
+        trailing_tables_block(a.qt, a.trail_k, a.T, a.MN, a.MX, part64, part32, a.tmax);
         break;
     }
 }
@@ -282,6 +283,7 @@ cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream
     a.T = T;
     a.MN = MN;
     a.MX = MX;
+    a.tmax = sc.ctr + CTR_TMAX;
     a.trail_k = trail_k;
     if (q.nw > 0) a.role[a.nroles++] = ROLE_WEIGHTS;
     if (q.tab_e || q.tab_xy) a.role[a.nroles++] = ROLE_PAIRTAB;

@@ -805,8 +805,9 @@ FS_D PairC pair_consts(const QueryConst& q)
 // block (any size; part64 / part32 hold blockDim.x entries).  Level P-1 is
 // summed over the pair's closed form; each further level (P-2 for k = 4) is
 // one more strided scan of the same tables in place.  See k_trailing_tables.
+// tmax (nullable, global): receives the largest entry of T (atomicMax).
 FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
-                                uint64_t* part64, int32_t* part32)
+                                uint64_t* part64, int32_t* part32, uint64_t* tmax = nullptr)
 {
     const int len = q.n + 1;
     for (int lvl = q.P - 1; lvl >= q.P + 2 - k; lvl--) {
@@ -848,6 +849,15 @@ FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t
             }
         }
         __syncthreads();
+    }
+    if (tmax) {
+        uint64_t m = 0;
+        for (int p = threadIdx.x; p < len; p += blockDim.x) m = T[p] > m ? T[p] : m;
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t y = __shfl_xor_sync(FULL, m, o);
+            m = y > m ? y : m;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)tmax, (unsigned long long)m);
     }
 }
 
