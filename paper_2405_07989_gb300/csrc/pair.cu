@@ -323,6 +323,10 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256) k_triple_walk(
     __shared__ unsigned long long bsum;
     __shared__ int bmin, bmax;
     extern __shared__ __align__(16) unsigned char dyn[];
+    if (!block_has_slices(sc)) {  // skips the table copy too
+        if (threadIdx.x == 0) publish_count(sc.ctr, dev_count);
+        return;
+    }
     load_smemq(q3, sq);
     if (threadIdx.x == 0) {
         bsum = 0;
@@ -433,7 +437,7 @@ cudaError_t launch_pair_slice_runs(const QueryConst& q, const Scratch& sc, const
 //   F = sum_{k <= P-1} (C_k[p_k] - C_k[p_k - a_k h_k]),
 // each term the factorizations whose level-k coordinate is below a_k.  Every
 // block builds W (leaf counts, for unranking) and C in shared memory (when
-// they fit), then its warps unrank slice starts (as k_plan) and write
+// they fit), then its threads unrank slice starts (as k_plan) and write
 // slice_off[s] = F(start of s) directly; the total is C_0[n].  The grid also
 // writes the pair tables the write walk reads.
 __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ QueryConst q,
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
     __shared__ int32_t hs[FS_MAX_D];
     __shared__ Div32 dvh[FS_MAX_D];
     __shared__ uint64_t sS, sL, sQ, sR;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int len = q.n + 1;
     const int P = q.P;
     uint64_t* Ws = (uint64_t*)dyn;               // (P-1) x (n+1) leaf counts
@@ -495,38 +499,28 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
     SliceSplit split;
     split.Q = sQ;
     split.R = sR;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + tid) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t s = gw; s < S; s += nw) {
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t* Clast = C + (size_t)(P - 1) * len;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + tid; s < S; s += nt) {
         int32_t* st = sc.starts + s * START_W;
         const uint64_t k0 = split.start(s);
         if (k0 >= L) {  // empty slice: starts at the end
-            if (lane == 0) {
-                st[START_W - 1] = -1;
-                sc.slice_off[s] = C[q.n];
-            }
+            st[START_W - 1] = -1;
+            sc.slice_off[s] = C[q.n];
             continue;
         }
-        RunPrefix rp;
-        const int32_t b = warp_unrank(q, hs, dvh, Ws, k0, lane, rp);
-        if (lane < P - 1) st[lane] = rp.a;
-        if (lane == 0) st[START_W - 1] = b;
-        // lane k < P-1 holds level k: a = rp.a, residual after it rp.r; before
-        // it, lane k-1's residual (n for level 0); level P-1 is (b, its run)
-        const int32_t after = rp.r;
-        int32_t before = __shfl_up_sync(FULL, after, 1);
-        if (lane == 0) before = q.n;
+        // level k < P-1 with residual p before it and coordinate a contributes
+        // C_k[p] - C_k[p - a h_k]; level P-1 (index b in the run with residual pr)
+        // C_{P-1}[pr] - C_{P-1}[pr - b h_{P-1}]
         uint64_t f = 0;
-        if (lane < P - 1) {
-            const uint64_t* Ck = C + (size_t)lane * len;
-            f = Ck[before] - Ck[after];
-        } else if (lane == P - 1) {
-            const uint64_t* Ck = C + (size_t)(P - 1) * len;
-            const int32_t pr = P >= 2 ? before : q.n;  // the run's residual
-            f = Ck[pr] - Ck[pr - b * hs[P - 1]];
-        }
-        f = warp_sum_u64(f);
-        if (lane == 0) sc.slice_off[s] = f;
+        int32_t pr;
+        const int32_t b = thread_unrank(q, hs, dvh, Ws, k0, pr, [&](int k, int32_t p, int32_t a) {
+            st[k] = a;
+            const uint64_t* Ck = C + (size_t)k * len;
+            f += Ck[p] - Ck[p - a * hs[k]];
+        });
+        st[START_W - 1] = b;
+        sc.slice_off[s] = f + Clast[pr] - Clast[pr - b * hs[P - 1]];
     }
 }
 
@@ -544,7 +538,7 @@ cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_
     int sms = 0;
     e = sm_count_cached(&sms);
     if (e != cudaSuccess) return e;
-    const uint64_t need = (S_req + 31) / 32;  // 32 warps per block
+    const uint64_t need = (S_req + 1023) / 1024;  // one slice per thread
     const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
     k_plan_offsets<<<blocks, 1024, smem, st>>>(q, sc, S_req, auto_s, min_leaves, dev_count);
     return cudaGetLastError();

@@ -80,7 +80,7 @@ constexpr size_t PLAN_SMEM_MAX = 160 * 1024;
 // The slice planner (Sec. 4, the role of Algorithm 4.1): S_req slices, or with
 // auto_s as many as keep about min_leaves leaves per slice (at most S_req);
 // writes the count and every slice's start (its first leaf, found by
-// warp_unrank on the exact leaf counts W).  One warp per slice, grid-stride.
+// thread_unrank on the exact leaf counts W).  One thread per slice, grid-stride.
 FS_D void plan_slices(const QueryConst& q, const Scratch& sc, const uint64_t* W, const int32_t* hs,
                       const Div32* dvh, uint64_t S_req, int auto_s, uint64_t min_leaves)
 {
@@ -108,20 +108,17 @@ FS_D void plan_slices(const QueryConst& q, const Scratch& sc, const uint64_t* W,
     SliceSplit split;
     split.Q = sQ;
     split.R = sR;
-    const int lane = threadIdx.x & 31;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t s = gw; s < S; s += nw) {
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += nt) {
         int32_t* st = sc.starts + s * START_W;
         const uint64_t k0 = split.start(s);
         if (k0 >= L) {
-            if (lane == 0) st[START_W - 1] = -1;
+            st[START_W - 1] = -1;
             continue;
         }
-        RunPrefix rp;
-        const int32_t b = warp_unrank(q, hs, dvh, W, k0, lane, rp);
-        if (lane < q.P - 1) st[lane] = rp.a;
-        if (lane == 0) st[START_W - 1] = b;
+        int32_t pr;
+        st[START_W - 1] = thread_unrank(q, hs, dvh, W, k0, pr,
+                                        [&](int k, int32_t, int32_t a) { st[k] = a; });
     }
 }
 
@@ -151,6 +148,14 @@ __global__ void __launch_bounds__(1024) k_plan_smem(const __grid_constant__ Quer
     if (threadIdx.x < FS_MAX_D) {
         hs[threadIdx.x] = q.h[threadIdx.x];
         dvh[threadIdx.x] = q.dv_h[threadIdx.x];
+    }
+    if (blockIdx.x > 0) {  // a block with no slice (one per thread) skips the copy
+        uint64_t S = S_req;
+        if (auto_s) {
+            const uint64_t want = (total_leaves(q, sc.W) + min_leaves - 1) / min_leaves;
+            S = want < S ? (want < 1 ? 1 : want) : S;
+        }
+        if ((uint64_t)blockIdx.x * blockDim.x >= S) return;
     }
     const uint32_t words = (uint32_t)q.nw * (uint32_t)(q.n + 1);
     const ulonglong2* src = (const ulonglong2*)sc.W;  // 256-byte aligned section
@@ -308,12 +313,12 @@ cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, 
         cudaError_t e = sm_count_cached(&sms);
         if (e == cudaSuccess) e = smem_optin((const void*)k_plan_smem, (int)wbytes);
         if (e != cudaSuccess) return e;
-        const uint64_t need = (S_req + 31) / 32;  // blocks of 32 warps, one per SM
+        const uint64_t need = (S_req + 1023) / 1024;  // one slice per thread, one block per SM
         const unsigned blocks = (unsigned)(need < (uint64_t)sms ? need : (uint64_t)sms);
         k_plan_smem<<<blocks, 1024, wbytes, st>>>(q, sc, S_req, auto_s, min_leaves);
         return cudaGetLastError();
     }
-    uint64_t blocks = (S_req + 7) / 8;  // one warp per slice
+    uint64_t blocks = (S_req + 255) / 256;  // one thread per slice
     if (blocks > 16384) blocks = 16384;
     if (blocks < 1) blocks = 1;
     k_plan<<<(unsigned)blocks, 256, 0, st>>>(q, sc, S_req, auto_s, min_leaves);

@@ -64,9 +64,12 @@ FS_D uint64_t sps_in(const uint64_t* in, int p, const Div32& dv_in)
     return in ? in[p] : (uint64_t)div32((uint32_t)p, dv_in) + 1;
 }
 
-// Few, short chains (a small table): one warp per chain, 32 consecutive chain
-// elements per step with a warp scan -- no block-wide barriers, which is what
-// the segmented form below spends its time on at this size.
+// Few, short chains (a small table): one warp per chain, no block-wide
+// barriers (which is what the segmented form below spends its time on at this
+// size).  A chain of up to 256 elements is scanned in one pass: lane l takes
+// the E = ceil(len_chain / 32) consecutive elements from l E on (their loads
+// all in flight at once), sums them, and a warp scan of the lane totals
+// places them.
 FS_D bool strided_by_warps(int len, int s)
 {
     return s <= 2 * (int)(blockDim.x >> 5) && (len - 1) / s + 1 <= 256;
@@ -75,21 +78,28 @@ FS_D bool strided_by_warps(int len, int s)
 template <class T, class Op, class In>
 FS_D void warp_chains_scan(In in, T* out, int len, int s, Op op, T ident)
 {
+    constexpr int EMAX = 8;  // 256 / 32
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int rho = threadIdx.x >> 5; rho < s; rho += nw) {
-        T carry = ident;
-        for (int t0 = 0;; t0 += 32) {
-            const long long p = rho + (long long)(t0 + lane) * s;
-            if (!__any_sync(FULL, p < len)) break;
-            T x = p < len ? in((int)p) : ident;
+        const int cl = (len - 1 - rho) / s + 1;  // elements rho, rho + s, .. below len
+        const int E = (cl + 31) >> 5;
+        const int t0 = lane * E;
+        T v[EMAX];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T y = __shfl_up_sync(FULL, x, o);
-                if (lane >= o) x = op(y, x);
-            }
-            if (p < len) out[p] = op(carry, x);
-            carry = op(carry, __shfl_sync(FULL, x, 31));
+        for (int j = 0; j < EMAX; j++) v[j] = (j < E && t0 + j < cl) ? in(rho + (t0 + j) * s) : ident;
+#pragma unroll
+        for (int j = 1; j < EMAX; j++) v[j] = op(v[j - 1], v[j]);
+        T x = v[EMAX - 1];  // this lane's total (ident past its elements)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x = op(y, x);
         }
+        T ex = __shfl_up_sync(FULL, x, 1);
+        if (lane == 0) ex = ident;
+#pragma unroll
+        for (int j = 0; j < EMAX; j++)
+            if (j < E && t0 + j < cl) out[rho + (t0 + j) * s] = op(ex, v[j]);
     }
     __syncthreads();
 }
@@ -281,6 +291,45 @@ FS_D int32_t warp_unrank(const QueryConst& q, const int32_t* hs, const Div32* dv
             rp.l = lsum;
         }
     }
+    return (int32_t)rho;
+}
+
+// The same search by one thread: a binary search per level (about
+// log2(p / h_k) probes), no warp cooperation.  A planner with many slices per
+// warp spends a few instructions per slice this way instead of a few hundred.
+// on_level(k, p, a) sees each prefix level k < P-1 with the residual p before
+// it and its coordinate a; the run residual (after level P-2, n if P = 1) goes
+// to p_run.  Returns a_{P-1}, the index inside the run.
+template <class OnLevel>
+FS_D int32_t thread_unrank(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                           const uint64_t* W, uint64_t rank, int32_t& p_run, OnLevel on_level)
+{
+    int32_t p = q.n;
+    uint64_t rho = rank;
+    const int np = q.P - 1;
+    for (int k = 0; k < np; k++) {
+        const uint64_t* Wk = W + (size_t)k * (size_t)(q.n + 1);
+        const int32_t h = hs[k];
+        const uint64_t top = Wk[p];
+        const uint64_t target = top - rho;  // >= 1
+        // W_k[p - x h] >= target holds at lo and fails at hi (hi one past the range)
+        int32_t lo = 0, hi = (int32_t)div32((uint32_t)p, dvh[k]) + 1;
+        uint64_t wlo = top;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            const uint64_t w = Wk[p - mid * h];
+            if (w >= target) {
+                lo = mid;
+                wlo = w;
+            } else {
+                hi = mid;
+            }
+        }
+        rho -= top - wlo;
+        on_level(k, p, lo);
+        p -= lo * h;
+    }
+    p_run = p;
     return (int32_t)rho;
 }
 
@@ -594,6 +643,18 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
     }
 }
 
+// Whether any warp of this block takes a slice in run_queue: its first warp's
+// static slice s_lo + (global warp index) is inside the window, or every later
+// warp's is not either (and the dynamic ones start past all warps).  Lets a
+// block skip its prologue (a shared-memory table copy) when the planner chose
+// fewer slices than the grid has warps.
+FS_D bool block_has_slices(const Scratch& sc)
+{
+    const uint64_t S_all = sc.ctr[CTR_SEFF];
+    const uint64_t S = sc.s_hi < S_all ? sc.s_hi : S_all;
+    return sc.s_lo + (uint64_t)blockIdx.x * (blockDim.x >> 5) < S;
+}
+
 // Called by thread 0 of every block of a count walk after it has added its
 // part to ctr[CTR_COUNT]: the last block to finish copies the total to
 // *dev_count (the caller's device memory), so no separate copy kernel runs.
@@ -804,7 +865,8 @@ FS_D PairC pair_consts(const QueryConst& q)
 // The trailing-k tables of q (k = 3 or 4) for p = 0..n, built by the calling
 // block (any size; part64 / part32 hold blockDim.x entries).  Level P-1 is
 // summed over the pair's closed form; each further level (P-2 for k = 4) is
-// one more strided scan of the same tables in place.  See k_trailing_tables.
+// one more strided scan of the same tables in place (the TRAIL role of
+// k_precompute).
 // tmax (nullable, global): receives the largest entry of T (atomicMax).
 FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
                                 uint64_t* part64, int32_t* part32, uint64_t* tmax = nullptr)
