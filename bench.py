@@ -433,7 +433,8 @@ COUNT_OPS_PER_LEAF = 8
 def heavy_count_extras(fs, workloads, dev):
     """Count and length statistics of the count-only heavy query (8 generators
     from seed 0, n = 40000, 7.66e12 factorizations), event-timed, with the
-    count walk's integer roofline against the probed add rate."""
+    count walk's integer roofline against the probed add rate; the counts of
+    the same draw at seeds 1 and 2 beside it."""
     import torch
     n, g = workloads.config3(0)
     rates = {name: fs.fs_probe_int_rate(k, 2048) for k, name in ((0, "add"), (1, "lop3"),
@@ -442,7 +443,7 @@ def heavy_count_extras(fs, workloads, dev):
     _, _, leaves = fs.fs_plan(n, g, 1, pair)
     dc = torch.zeros(1, dtype=torch.int64, device=dev)
 
-    def timed_count(cfg, walk):
+    def timed_count(cfg, walk, n=n, g=g):
         fs.fs_count_async(n, g, dc, cfg)
         torch.cuda.synchronize()
         fs.fs_profile_read()
@@ -470,6 +471,19 @@ def heavy_count_extras(fs, workloads, dev):
     t0 = time.perf_counter()
     assert fs.fs_length_stats(n, g, None) == (cnt, mn, mx)
     len_minmax_s = time.perf_counter() - t0
+    # the same draw at seeds 1 and 2: every walk, the same count
+    seeds = {}
+    for seed in (1, 2):
+        ns, gs = workloads.config3(seed)
+        _, _, lv = fs.fs_plan(ns, gs, 1, pair)
+        zs, mss, wms, _ = timed_count(pair, "pair_count", ns, gs)
+        z3, ms3s, _, _ = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count", ns, gs)
+        z4, ms4s, _, _ = timed_count(None, "quad_count", ns, gs)
+        assert z3 == zs and z4 == zs
+        seeds[str(seed)] = {"gens": list(gs), "n": ns, "factorizations": zs, "leaves": lv,
+                            "count_ms": mss, "count_leaves_per_s": lv / (wms / 1000.0),
+                            "count_roofline_frac": lv * COUNT_OPS_PER_LEAF / (wms / 1000.0) / rates["add"],
+                            "count_triple_ms": ms3s, "count_quad_ms": ms4s}
     return {
         "workload": f"count-only heavy query g={tuple(g)}, n={n}",
         "factorizations": Z, "leaves": leaves, "count_ms": ms, "count_walk_ms": walk_ms,
@@ -487,6 +501,7 @@ def heavy_count_extras(fs, workloads, dev):
         "length_stats_s": len_s, "length_min_max": [mn, mx],
         "length_factorizations_per_s": Z / len_s,
         "length_min_max_only_s": len_minmax_s,
+        "other_seeds": seeds,
     }
 
 

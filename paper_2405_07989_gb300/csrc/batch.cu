@@ -164,6 +164,7 @@ struct BatchCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = false;
+    static constexpr bool PACKED = true;
     FS_D void fault()
     {
         if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[BCTR_ERR], 1ull);

@@ -32,6 +32,7 @@ struct EnumFix {
 
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
+    static constexpr bool PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int, int32_t a2)
     {

@@ -21,6 +21,7 @@ struct CountCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
+    static constexpr bool PACKED = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -82,6 +83,7 @@ struct LenCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
+    static constexpr bool PACKED = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -205,6 +207,7 @@ struct AnyCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
+    static constexpr bool PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t a2)
     {
@@ -281,6 +284,7 @@ struct TripleCons {
     int32_t mn, mx;
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
+    static constexpr bool PACKED = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}

@@ -401,6 +401,10 @@ FS_D int32_t warp_load_start(const QueryConst& q, const int32_t* hs, const int32
 //   static constexpr bool SKIP    -- visit only the leaves that common-divisor
 //                                    skipping keeps (for consumers whose per-leaf
 //                                    work outweighs the per-run class arithmetic)
+//   static constexpr bool PACKED  -- the lanes of one step may hold leaves of
+//                                    different sibling runs (walk_slice_packed;
+//                                    run_begin is then not called and chunk gets
+//                                    each lane's own a and lp)
 //   void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)
 //       -- a new run starts (warp-uniform); its prefix is rp.a on lanes
 //          0..P-3 and a2 at level P-2 (rp.a of lane P-2 is stale);
@@ -440,11 +444,137 @@ FS_D void skip_class(const QueryConst& q, uint32_t R, uint32_t b, uint32_t nh, u
     cnt = off < nh ? div32(nh - 1 - off, q.dv_skm[0]) + 1 : 0;
 }
 
+// The same walk for consumers that do not depend on the order of the leaves
+// inside a slice (Cons::PACKED: counts, length statistics).  Lane j first works
+// out which of run j's leaves the slice takes (a scan of the run lengths) and
+// which of those the walk visits (skip_class).  Then each run's full 32-leaf
+// steps are taken run by run, as in walk_slice, and the remainders of all runs
+// of the group (fewer than 32 leaves each) are packed into shared steps: lane
+// l of such a step finds its run by a 5-step search over the runs' offsets.
+// Short runs no longer cost a step each, and the per-run bookkeeping is done
+// once per group by all lanes together.
+template <class Cons>
+FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                            const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
+                            int32_t hk, Cons& cons)
+{
+    RunPrefix rp;
+    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
+    const int np = q.P - 1;
+    const uint32_t hin = (uint32_t)hs[np];
+    const bool skip = Cons::SKIP && (q.sk_m[0] > 1 || q.sk_g[0] > 1);
+    const uint32_t ma = skip ? (uint32_t)q.sk_m[0] : 1u;  // step of a between visited leaves
+    const uint32_t mstep = ma * hin;
+    uint64_t rem = nleaves;
+    for (;;) {
+        int32_t Rc = q.n, lpc = 0, ac = 0;
+        uint32_t hsib = 0, nsib = 1;
+        if (np > 0) {
+            Rc = __shfl_sync(FULL, rp.r, np - 1);
+            lpc = __shfl_sync(FULL, rp.l, np - 1);
+            ac = __shfl_sync(FULL, rp.a, np - 1);
+            hsib = (uint32_t)hs[np - 1];
+            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            if (nsib > 32) nsib = 32;
+        }
+        // lane j: sibling run j, residual R_j = Rc - j hsib, leaves from b_j on
+        const bool act = (uint32_t)lane < nsib;
+        const uint32_t Rj = (uint32_t)Rc - (uint32_t)lane * hsib;
+        const uint32_t bj = lane == 0 ? (uint32_t)b : 0u;
+        const uint32_t left = act ? div32(Rj, q.dv_in) + 1 - bj : 0u;
+        uint64_t ir = left;  // leaves of runs 0..j
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, ir, o);
+            if (lane >= o) ir += t;
+        }
+        // take the runs whose leaves so far stay below 2^31 (at least one), so
+        // the visited-leaf offsets below fit 32 bits
+        uint32_t ns = __popc(__ballot_sync(FULL, act && ir < (1ull << 31)));
+        if (ns == 0) ns = 1;
+        const uint64_t er = ir - left;
+        uint32_t nh = 0;  // leaves of run j in the slice
+        if ((uint32_t)lane < ns && er < rem) nh = rem - er < (uint64_t)left ? (uint32_t)(rem - er) : left;
+        uint32_t first = bj, cnt = nh, mj = 1;
+        if (skip && nh > 0) skip_class(q, Rj, bj, nh, first, cnt, mj);
+        const uint32_t nfull = cnt >> 5, part = cnt & 31;
+        // the full steps, run by run: lane l takes the run's leaves l, l + 32, ..
+        for (uint32_t m = __ballot_sync(FULL, nfull > 0); m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const uint32_t nf = __shfl_sync(FULL, nfull, j);
+            uint32_t a = __shfl_sync(FULL, first, j) + (uint32_t)lane * ma;
+            uint32_t r = __shfl_sync(FULL, Rj, j) - a * hin;
+            const int32_t lp = lpc + j;
+            uint32_t i = 0;
+            if (Cons::UNROLL > 1) {
+                for (; i + Cons::UNROLL <= nf; i += Cons::UNROLL) {
+#pragma unroll
+                    for (int u = 0; u < Cons::UNROLL; u++) {
+                        if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                        r -= 32u * mstep;
+                        a += 32u * ma;
+                    }
+                }
+            }
+            for (; i < nf; i++) {
+                if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                r -= 32u * mstep;
+                a += 32u * ma;
+            }
+        }
+        // the remainders, packed: run j's last `part` visited leaves
+        const uint32_t pa = first + (cnt - part) * ma;  // the first of them
+        const uint32_t r0 = Rj - pa * hin;
+        uint32_t iv = part;  // remainder leaves of runs 0..j
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, iv, o);
+            if (lane >= o) iv += t;
+        }
+        const uint32_t ev = iv - part;
+        const uint32_t tot = __shfl_sync(FULL, iv, 31);
+        for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+            const uint32_t t = t0 + (uint32_t)lane;
+            // the run of visited leaf t: the last j with ev_j <= t (runs past
+            // the group's end have ev_j = tot)
+            int j = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const uint32_t e = __shfl_sync(FULL, ev, j + st);
+                if (e <= t) j += st;
+            }
+            const uint32_t k = t - __shfl_sync(FULL, ev, j);
+            const uint32_t a = __shfl_sync(FULL, pa, j) + k * ma;
+            const uint32_t r = __shfl_sync(FULL, r0, j) - k * mstep;
+            if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lpc + j)) return true;
+        }
+        const uint64_t took = __shfl_sync(FULL, ir, (int)ns - 1);
+        if (took >= rem) return false;
+        rem -= took;
+        b = 0;
+        // the last run taken becomes the current one; step to its lex successor
+        if (np == 0) {
+            cons.fault();  // the slice claims leaves past the last one
+            return false;
+        }
+        if (lane == np - 1) {
+            rp.a = ac + (int32_t)ns - 1;
+            rp.r = (int32_t)((uint32_t)Rc - (ns - 1) * hsib);
+            rp.l = lpc + (int32_t)ns - 1;
+        }
+        if (!warp_next_run(q, lane, hk, rp)) {
+            cons.fault();
+            return false;
+        }
+    }
+}
+
 template <class Cons>
 FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                      const int32_t* starts, uint64_t s, uint64_t nleaves, int lane, int32_t hk,
                      Cons& cons)
 {
+    if constexpr (Cons::PACKED) return walk_slice_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
     RunPrefix rp;
     int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
     const int np = q.P - 1;
