@@ -165,6 +165,7 @@ struct BatchCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = false;
     static constexpr bool PACKED = true;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault()
     {
         if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[BCTR_ERR], 1ull);

@@ -39,6 +39,7 @@ struct EnumCons {
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
     static constexpr bool PACKED = false;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
 
     FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)

@@ -29,10 +29,12 @@ struct EnumFix {
     uint64_t* ctr;
     int32_t piece;
     int32_t pre[NP > 0 ? NP : 1];
+    int32_t a2base, lpbase;  // LEX_PACKED: level P-2 and prefix sum of the group's first run
 
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
     static constexpr bool PACKED = false;
+    static constexpr bool LEX_PACKED = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int, int32_t a2)
     {
@@ -42,17 +44,30 @@ struct EnumFix {
             pre[k] = k == NP - 1 ? a2 : v;
         }
     }
+    FS_D void group_begin(const QueryConst&, const RunPrefix& rp, int, int32_t ac, int32_t lpc)
+    {
+#pragma unroll
+        for (int k = 0; k < NP - 1; k++) pre[k] = __shfl_sync(FULL, rp.a, k);
+        a2base = ac;
+        lpbase = lpc;
+    }
+    // level P-2 of this lane's leaf
+    FS_D int32_t level2(int32_t lp) const
+    {
+        if constexpr (NP == 0) return 0;
+        else return LEX_PACKED ? a2base + (lp - lpbase) : pre[NP - 1];
+    }
     FS_D void slice_begin(const QueryConst&, uint64_t s)
     {
         sg.begin(slice_off[s] + (blk ? blk[s / SLICE_GROUP] : 0ull));
     }
     FS_D void slice_end(const QueryConst&, uint64_t) { sg.flush(); }
 
-    FS_D void put_row(ELEM* row, int32_t a, int32_t x, int32_t y) const
+    FS_D void put_row(ELEM* row, int32_t a2, int32_t a, int32_t x, int32_t y) const
     {
         int32_t lev[D];
 #pragma unroll
-        for (int k = 0; k < NP; k++) lev[k] = pre[k];
+        for (int k = 0; k < NP; k++) lev[k] = k == NP - 1 ? a2 : pre[k];
         lev[NP] = a;
         lev[NP + 1] = x;
         lev[NP + 2] = y;
@@ -78,7 +93,7 @@ struct EnumFix {
     // leaf of more than LEAF_ROWS_MAX rows, where one lane per leaf would idle
     // the others.
     FS_D void emit_one(const QueryConst& q, int lane, uint32_t cs, int32_t xs, int32_t ys,
-                       int32_t as)
+                       int32_t as, int32_t a2s)
     {
         for (uint32_t t0 = 0; t0 < cs; t0 += (uint32_t)piece) {
             const uint32_t npc = min((uint32_t)piece, cs - t0);
@@ -88,15 +103,16 @@ struct EnumFix {
                 const uint32_t k = j + lane;
                 if (k < npc) {
                     const int32_t t = (int32_t)(t0 + k);
-                    put_row(sb + k * D, as, xs + t * q.v, ys - t * q.u);
+                    put_row(sb + k * D, a2s, as, xs + t * q.v, ys - t * q.u);
                 }
             }
             sg.nst += (int32_t)npc;
         }
     }
 
-    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t)
+    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t lp)
     {
+        const int32_t a2 = level2(lp);
         int32_t x0 = 0, y0 = 0;
         uint32_t c = 0;
         if (valid) c = pair_xy<true>(q, X0, YD, r, x0, y0);
@@ -106,7 +122,8 @@ struct EnumFix {
                 const int32_t xs = __shfl_sync(FULL, x0, src);
                 const int32_t ys = __shfl_sync(FULL, y0, src);
                 const int32_t as = __shfl_sync(FULL, a, src);
-                if (cs) emit_one(q, lane, cs, xs, ys, as);
+                const int32_t a2s = __shfl_sync(FULL, a2, src);
+                if (cs) emit_one(q, lane, cs, xs, ys, as, a2s);
             }
             return false;
         }
@@ -126,7 +143,7 @@ struct EnumFix {
             const uint32_t lo = max(excl, ps), hi = min(incl, ps + npc);
             int32_t t = (int32_t)(lo - excl);
             for (uint32_t i = lo; i < hi; i++, t++)
-                put_row(sb + (i - ps) * D, a, x0 + t * q.v, y0 - t * q.u);
+                put_row(sb + (i - ps) * D, a2, a, x0 + t * q.v, y0 - t * q.u);
             sg.nst += (int32_t)npc;
         }
         return false;
@@ -166,6 +183,8 @@ __global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant_
     cons.piece = (Stager<ELEM>::STG - Stager<ELEM>::VEC) / D;
 #pragma unroll
     for (int k = 0; k < C::NP; k++) cons.pre[k] = 0;
+    cons.a2base = 0;
+    cons.lpbase = 0;
     run_queue(q, sq, sc, queue, cons);
     cons.sg.finish();
 }

@@ -22,6 +22,7 @@ struct CountCons {
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
     static constexpr bool PACKED = true;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -84,6 +85,7 @@ struct LenCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
     static constexpr bool PACKED = true;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -208,6 +210,7 @@ struct AnyCons {
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
     static constexpr bool PACKED = false;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t a2)
     {
@@ -285,6 +288,7 @@ struct TripleCons {
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
     static constexpr bool PACKED = true;
+    static constexpr bool LEX_PACKED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}

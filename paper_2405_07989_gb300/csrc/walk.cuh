@@ -569,12 +569,105 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
     }
 }
 
+// The walk in lex order with the leaves of a sibling group packed (for a
+// consumer that needs the order, Cons::LEX_PACKED): the warp steps through the
+// group's visited leaves 32 at a time in lex order, whatever run each belongs
+// to; lane l finds the run of its leaf by a 5-step search over the runs'
+// offsets.  cons.group_begin(q, rp, lane, ac, lpc) starts each group (its runs
+// have level P-2 = ac + j and prefix sum lpc + j, j = 0, 1, ..); chunk gets
+// each lane's own a and lp.
+template <class Cons>
+FS_D bool walk_slice_lex_packed(const QueryConst& q, const int32_t* hs, const Div32* dvh,
+                                const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
+                                int32_t hk, Cons& cons)
+{
+    RunPrefix rp;
+    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
+    const int np = q.P - 1;
+    const uint32_t hin = (uint32_t)hs[np];
+    const bool skip = Cons::SKIP && (q.sk_m[0] > 1 || q.sk_g[0] > 1);
+    const uint32_t ma = skip ? (uint32_t)q.sk_m[0] : 1u;
+    const uint32_t mstep = ma * hin;
+    uint64_t rem = nleaves;
+    for (;;) {
+        int32_t Rc = q.n, lpc = 0, ac = 0;
+        uint32_t hsib = 0, nsib = 1;
+        if (np > 0) {
+            Rc = __shfl_sync(FULL, rp.r, np - 1);
+            lpc = __shfl_sync(FULL, rp.l, np - 1);
+            ac = __shfl_sync(FULL, rp.a, np - 1);
+            hsib = (uint32_t)hs[np - 1];
+            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            if (nsib > 32) nsib = 32;
+        }
+        const bool act = (uint32_t)lane < nsib;
+        const uint32_t Rj = (uint32_t)Rc - (uint32_t)lane * hsib;
+        const uint32_t bj = lane == 0 ? (uint32_t)b : 0u;
+        const uint32_t left = act ? div32(Rj, q.dv_in) + 1 - bj : 0u;
+        uint64_t ir = left;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, ir, o);
+            if (lane >= o) ir += t;
+        }
+        uint32_t ns = __popc(__ballot_sync(FULL, act && ir < (1ull << 31)));
+        if (ns == 0) ns = 1;
+        const uint64_t er = ir - left;
+        uint32_t nh = 0;
+        if ((uint32_t)lane < ns && er < rem) nh = rem - er < (uint64_t)left ? (uint32_t)(rem - er) : left;
+        uint32_t first = bj, cnt = nh, mj = 1;
+        if (skip && nh > 0) skip_class(q, Rj, bj, nh, first, cnt, mj);
+        uint32_t iv = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, iv, o);
+            if (lane >= o) iv += t;
+        }
+        const uint32_t ev = iv - cnt;
+        const uint32_t tot = __shfl_sync(FULL, iv, 31);
+        const uint32_t r0 = Rj - first * hin;
+        cons.group_begin(q, rp, lane, ac, lpc);
+        for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+            const uint32_t t = t0 + (uint32_t)lane;
+            int j = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const uint32_t e = __shfl_sync(FULL, ev, j + st);
+                if (e <= t) j += st;
+            }
+            const uint32_t k = t - __shfl_sync(FULL, ev, j);
+            const uint32_t a = __shfl_sync(FULL, first, j) + k * ma;
+            const uint32_t r = __shfl_sync(FULL, r0, j) - k * mstep;
+            if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lpc + j)) return true;
+        }
+        const uint64_t took = __shfl_sync(FULL, ir, (int)ns - 1);
+        if (took >= rem) return false;
+        rem -= took;
+        b = 0;
+        if (np == 0) {
+            cons.fault();
+            return false;
+        }
+        if (lane == np - 1) {
+            rp.a = ac + (int32_t)ns - 1;
+            rp.r = (int32_t)((uint32_t)Rc - (ns - 1) * hsib);
+            rp.l = lpc + (int32_t)ns - 1;
+        }
+        if (!warp_next_run(q, lane, hk, rp)) {
+            cons.fault();
+            return false;
+        }
+    }
+}
+
 template <class Cons>
 FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                      const int32_t* starts, uint64_t s, uint64_t nleaves, int lane, int32_t hk,
                      Cons& cons)
 {
     if constexpr (Cons::PACKED) return walk_slice_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
+    if constexpr (Cons::LEX_PACKED)
+        return walk_slice_lex_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
     RunPrefix rp;
     int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
     const int np = q.P - 1;
