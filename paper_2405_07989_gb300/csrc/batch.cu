@@ -164,13 +164,12 @@ struct BatchCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = false;
-    static constexpr bool PACKED = true;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = true;
     FS_D void fault()
     {
         if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[BCTR_ERR], 1ull);
     }
-    FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
+    FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D bool chunk(const QueryConst&, int, bool valid, int32_t r, int32_t a, int32_t lp)
     {
         if (!valid) return false;

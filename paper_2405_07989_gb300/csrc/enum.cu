@@ -35,26 +35,28 @@ struct EnumCons {
     int32_t cin, cA, cB;   // columns of level P-1 and of the pair (-1: virtual)
     int32_t col[NR];
     int32_t pre[NR];
+    int32_t a2base, lpbase;  // level P-2 and prefix sum of the sibling group's first run
 
-    static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
-    static constexpr bool PACKED = false;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = false;
     FS_D void fault() { flag_fault(ctr); }
 
-    FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)
+    // the levels above P-2 are the group's; level P-2 differs by lane (a2)
+    FS_D void group_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t ac, int32_t lpc)
     {
         if constexpr (REGS) {
 #pragma unroll
             for (int k = 0; k < NR; k++) {
                 const int32_t v = __shfl_sync(FULL, rp.a, k);
-                pre[k] = k == np - 1 ? a2 : v;
+                if (k < np - 1) pre[k] = v;
             }
         } else {
-            __syncwarp();  // earlier rows have read the previous run's prefix
-            if (lane < np) tmpl[lane] = lane == np - 1 ? a2 : rp.a;
+            __syncwarp();  // earlier rows have read the previous group's prefix
+            if (lane < np - 1) tmpl[lane] = rp.a;
             __syncwarp();
         }
+        a2base = ac;
+        lpbase = lpc;
     }
 
     FS_D void slice_begin(const QueryConst&, uint64_t s)
@@ -65,7 +67,7 @@ struct EnumCons {
 
     // Rows [excl, incl) of this chunk belong to this lane's leaf; T rows in all.
     FS_D void emit(const QueryConst& q, int lane, uint32_t T, uint32_t excl, uint32_t incl,
-                   int32_t x0, int32_t y0, int32_t a)
+                   int32_t x0, int32_t y0, int32_t a, int32_t a2)
     {
         const int d = sg.d;
         for (uint32_t ps = 0; ps < T; ps += (uint32_t)piece) {
@@ -83,17 +85,18 @@ struct EnumCons {
                 const int32_t xs = __shfl_sync(FULL, x0, src);
                 const int32_t ys = __shfl_sync(FULL, y0, src);
                 const int32_t as = __shfl_sync(FULL, a, src);
+                const int32_t a2s = __shfl_sync(FULL, a2, src);
                 if (ok) {
                     const int32_t t = (int32_t)(ps + i - es);
                     ELEM* row = sb + i * d;
                     if constexpr (REGS) {
 #pragma unroll
                         for (int k = 0; k < NR; k++)
-                            if (k < np && col[k] >= 0) row[col[k]] = (ELEM)pre[k];
+                            if (k < np && col[k] >= 0) row[col[k]] = (ELEM)(k == np - 1 ? a2s : pre[k]);
                     } else {
                         for (int k = 0; k < np; k++) {
                             const int c = scol[k];
-                            if (c >= 0) row[c] = (ELEM)tmpl[k];
+                            if (c >= 0) row[c] = (ELEM)(k == np - 1 ? a2s : tmpl[k]);
                         }
                     }
                     if (cin >= 0) row[cin] = (ELEM)as;
@@ -106,8 +109,9 @@ struct EnumCons {
         }
     }
 
-    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t)
+    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t lp)
     {
+        const int32_t a2 = a2base + (lp - lpbase);
         int32_t x0 = 0, y0 = 0;
         uint32_t c = 0;
         if (valid) c = pair_xy<TAB>(q, X0, YD, r, x0, y0);
@@ -117,7 +121,7 @@ struct EnumCons {
                 const uint32_t cs = __shfl_sync(FULL, c, src);
                 if (cs == 0) continue;
                 const bool me = lane == src;
-                emit(q, lane, cs, me ? 0u : cs, cs, x0, y0, a);
+                emit(q, lane, cs, me ? 0u : cs, cs, x0, y0, a, a2);
             }
             return false;
         }
@@ -128,7 +132,7 @@ struct EnumCons {
             if (lane >= o) incl += t;
         }
         const uint32_t T = __shfl_sync(FULL, incl, 31);
-        if (T > 0) emit(q, lane, T, incl - c, incl, x0, y0, a);
+        if (T > 0) emit(q, lane, T, incl - c, incl, x0, y0, a, a2);
         return false;
     }
 };

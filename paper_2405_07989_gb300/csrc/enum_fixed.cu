@@ -29,21 +29,11 @@ struct EnumFix {
     uint64_t* ctr;
     int32_t piece;
     int32_t pre[NP > 0 ? NP : 1];
-    int32_t a2base, lpbase;  // LEX_PACKED: level P-2 and prefix sum of the group's first run
+    int32_t a2base, lpbase;  // level P-2 and prefix sum of the sibling group's first run
 
-    static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
-    static constexpr bool PACKED = false;
-    static constexpr bool LEX_PACKED = true;
+    static constexpr bool ANY_ORDER = false;
     FS_D void fault() { flag_fault(ctr); }
-    FS_D void run_begin(const QueryConst&, const RunPrefix& rp, int, int32_t a2)
-    {
-#pragma unroll
-        for (int k = 0; k < NP; k++) {
-            const int32_t v = __shfl_sync(FULL, rp.a, k);
-            pre[k] = k == NP - 1 ? a2 : v;
-        }
-    }
     FS_D void group_begin(const QueryConst&, const RunPrefix& rp, int, int32_t ac, int32_t lpc)
     {
 #pragma unroll
@@ -55,7 +45,7 @@ struct EnumFix {
     FS_D int32_t level2(int32_t lp) const
     {
         if constexpr (NP == 0) return 0;
-        else return LEX_PACKED ? a2base + (lp - lpbase) : pre[NP - 1];
+        else return a2base + (lp - lpbase);
     }
     FS_D void slice_begin(const QueryConst&, uint64_t s)
     {

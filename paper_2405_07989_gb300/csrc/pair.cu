@@ -21,10 +21,9 @@ struct CountCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
-    static constexpr bool PACKED = true;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = true;
     FS_D void fault() { flag_fault(ctr); }
-    FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
+    FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
     FS_D void slice_end(const QueryConst&, uint64_t s)
     {
@@ -84,10 +83,9 @@ struct LenCons {
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
-    static constexpr bool PACKED = true;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = true;
     FS_D void fault() { flag_fault(ctr); }
-    FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
+    FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
     FS_D void slice_end(const QueryConst&, uint64_t) {}
     FS_D bool chunk(const QueryConst& q, int, bool valid, int32_t r, int32_t a, int32_t lp)
@@ -204,29 +202,31 @@ struct AnyCons {
     const int32_t* YD;
     const PredConst* pc;
     unsigned long long* flag;
-    int64_t pw;  // weighted sum of the current run's prefix
+    int64_t pwb;  // weighted sum of the sibling group's first run prefix
+    int32_t lpb;  // its prefix sum (a lane's run is lp - lpb runs further)
     int poll;
     uint64_t* ctr;
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
-    static constexpr bool PACKED = false;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = true;
     FS_D void fault() { flag_fault(ctr); }
-    FS_D void run_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t a2)
+    FS_D void group_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t ac, int32_t lpc)
     {
         int64_t v = (lane < q.P - 2) ? pc->w[lane] * (int64_t)rp.a : 0;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        pw = v + (q.P >= 2 ? pc->w[q.P - 2] * (int64_t)a2 : 0);
+        pwb = v + (q.P >= 2 ? pc->w[q.P - 2] * (int64_t)ac : 0);
+        lpb = lpc;
     }
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
     FS_D void slice_end(const QueryConst&, uint64_t) {}
-    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t)
+    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t a, int32_t lp)
     {
         bool f = false;
         if (valid) {
             int32_t x0 = 0, y0 = 0;
             uint32_t c = pair_xy<TAB>(q, X0, YD, r, x0, y0);
             if (c > 0) {
+                const int64_t pw = pwb + (q.P >= 2 ? pc->w[q.P - 2] * (int64_t)(lp - lpb) : 0);
                 int64_t V0 = pw + pc->w[q.P - 1] * (int64_t)a +
                              pc->w[q.P] * (int64_t)x0 + pc->w[q.P + 1] * (int64_t)y0;
                 f = pred_on_progression(*pc, V0, c);
@@ -248,7 +248,7 @@ struct AnyCons {
 };
 
 template <bool TAB>
-__global__ void __launch_bounds__(256) k_pair_any(const __grid_constant__ QueryConst q,
+__global__ void __launch_bounds__(256, 4) k_pair_any(const __grid_constant__ QueryConst q,
                                                   Scratch sc, int queue,
                                                   const __grid_constant__ PredConst pred)
 {
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(256) k_pair_any(const __grid_constant__ QueryC
             YD[i] = sc.YD[i];
         }
     __syncthreads();
-    AnyCons<TAB> cons{X0, YD, &spc, (unsigned long long*)&sc.ctr[CTR_FOUND], 0, 0, sc.ctr};
+    AnyCons<TAB> cons{X0, YD, &spc, (unsigned long long*)&sc.ctr[CTR_FOUND], 0, 0, 0, sc.ctr};
     run_queue(q, sq, sc, queue, cons);
 }
 
@@ -287,10 +287,9 @@ struct TripleCons {
     int32_t mn, mx;
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
-    static constexpr bool PACKED = true;
-    static constexpr bool LEX_PACKED = false;
+    static constexpr bool ANY_ORDER = true;
     FS_D void fault() { flag_fault(ctr); }
-    FS_D void run_begin(const QueryConst&, const RunPrefix&, int, int32_t) {}
+    FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
     FS_D void slice_end(const QueryConst&, uint64_t s)
     {
@@ -323,7 +322,7 @@ struct TripleCons {
 // largest entry, recorded by the precompute, fits), so the lookups of the walk
 // hit shared memory instead of L2.
 template <int MODE, bool PER_SLICE, bool SMEMT>
-__global__ void __launch_bounds__(SMEMT ? 1024 : 256) k_triple_walk(
+__global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_walk(
     const __grid_constant__ QueryConst q3, Scratch sc, int queue, const uint64_t* T3,
     const int32_t* MN3, const int32_t* MX3, uint64_t* dev_count)
 {

@@ -390,29 +390,34 @@ FS_D int32_t warp_load_start(const QueryConst& q, const int32_t* hs, const int32
 }
 
 // ---------------------------------------------------------------------------
-// The slice walk: the slice's leaves in lex order, run by run.  Within a run
-// (fixed prefix of levels 0..P-2, residual R) the leaves are a_{P-1} = b, b+1,
-// ..., and lane l of a 32-leaf step takes a_{P-1} = b + 32 i + l, residual
-// R - a_{P-1} h_{P-1}; the last step of a run is masked.  Runs that differ only
-// in level P-2 ("siblings") are taken 32 at a time: lane j holds the residual
-// of sibling j, so the lex successor (a ballot over the levels) runs once per
-// group of siblings instead of once per run.  Cons must provide
-//   static constexpr int UNROLL   -- full 32-leaf steps per loop trip
+// The slice walk.  A run is the sequence of leaves a_{P-1} = b, b+1, ... under
+// one prefix of levels 0..P-2 (residual R; leaf a has residual R - a h_{P-1}).
+// Runs that differ only in level P-2 ("siblings") are taken 32 at a time: lane
+// j holds sibling j, so the lex successor of the prefix (a ballot over the
+// levels) runs once per group of siblings.  Lane j works out which of run j's
+// leaves the slice takes (a warp scan of the run lengths) and which of those
+// are visited (common-divisor skipping), then the warp visits the group's leaves
+// 32 per step in one of two ways (walk_slice_packed, walk_slice_lex_packed).
+// Cons must provide
+//   static constexpr bool ANY_ORDER -- the consumer does not depend on the
+//                                    order of the leaves (counts, lengths,
+//                                    predicates): full 32-leaf steps run by run,
+//                                    then the runs' remainders packed; else the
+//                                    group's leaves packed in lex order
+//   static constexpr int UNROLL   -- full 32-leaf steps per loop trip (ANY_ORDER)
 //   static constexpr bool SKIP    -- visit only the leaves that common-divisor
 //                                    skipping keeps (for consumers whose per-leaf
 //                                    work outweighs the per-run class arithmetic)
-//   static constexpr bool PACKED  -- the lanes of one step may hold leaves of
-//                                    different sibling runs (walk_slice_packed;
-//                                    run_begin is then not called and chunk gets
-//                                    each lane's own a and lp)
-//   void run_begin(const QueryConst&, const RunPrefix& rp, int lane, int32_t a2)
-//       -- a new run starts (warp-uniform); its prefix is rp.a on lanes
-//          0..P-3 and a2 at level P-2 (rp.a of lane P-2 is stale);
+//   void group_begin(const QueryConst&, const RunPrefix& rp, int lane,
+//                    int32_t ac, int32_t lpc)
+//       -- a sibling group starts (warp-uniform): levels 0..P-3 are rp.a on
+//          lanes 0..P-3; its runs have level P-2 = ac + j and prefix sum lpc + j
 //   bool chunk(const QueryConst&, int lane, bool valid, int32_t r, int32_t a,
 //              int32_t lp)
 //       -- one leaf per lane: residual r left for the pair, a = a_{P-1},
-//          lp = sum of the run prefix; invalid lanes must not use r; returns
-//          true to stop the walk (warp-uniform);
+//          lp = sum of the leaf's run prefix (so its run is lp - lpc siblings
+//          into the group); invalid lanes must not use r; returns true to stop
+//          the walk (warp-uniform);
 //   void fault() -- the slice ran past the last leaf (a planner fault).
 // Returns true if the consumer stopped the walk.
 // ---------------------------------------------------------------------------
@@ -444,15 +449,14 @@ FS_D void skip_class(const QueryConst& q, uint32_t R, uint32_t b, uint32_t nh, u
     cnt = off < nh ? div32(nh - 1 - off, q.dv_skm[0]) + 1 : 0;
 }
 
-// The same walk for consumers that do not depend on the order of the leaves
-// inside a slice (Cons::PACKED: counts, length statistics).  Lane j first works
-// out which of run j's leaves the slice takes (a scan of the run lengths) and
-// which of those the walk visits (skip_class).  Then each run's full 32-leaf
-// steps are taken run by run, as in walk_slice, and the remainders of all runs
-// of the group (fewer than 32 leaves each) are packed into shared steps: lane
-// l of such a step finds its run by a 5-step search over the runs' offsets.
-// Short runs no longer cost a step each, and the per-run bookkeeping is done
-// once per group by all lanes together.
+// The walk for consumers that do not depend on the order of the leaves inside
+// a slice (Cons::ANY_ORDER: counts, length statistics, predicates).  Each run's
+// full 32-leaf steps are taken run by run (lane l takes the run's leaves l,
+// l + 32, ..), then the remainders of all runs of the group (fewer than 32
+// leaves each) are packed into shared steps: lane l of such a step finds its
+// run by a 5-step search over the runs' offsets.  Short runs no longer cost a
+// step each, and the per-run bookkeeping is done once per group by all lanes
+// together.
 template <class Cons>
 FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                             const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
@@ -498,6 +502,7 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
         uint32_t first = bj, cnt = nh, mj = 1;
         if (skip && nh > 0) skip_class(q, Rj, bj, nh, first, cnt, mj);
         const uint32_t nfull = cnt >> 5, part = cnt & 31;
+        cons.group_begin(q, rp, lane, ac, lpc);
         // the full steps, run by run: lane l takes the run's leaves l, l + 32, ..
         for (uint32_t m = __ballot_sync(FULL, nfull > 0); m; m &= m - 1) {
             const int j = __ffs(m) - 1;
@@ -570,7 +575,7 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
 }
 
 // The walk in lex order with the leaves of a sibling group packed (for a
-// consumer that needs the order, Cons::LEX_PACKED): the warp steps through the
+// consumer that needs the order: enumerate): the warp steps through the
 // group's visited leaves 32 at a time in lex order, whatever run each belongs
 // to; lane l finds the run of its leaf by a 5-step search over the runs'
 // offsets.  cons.group_begin(q, rp, lane, ac, lpc) starts each group (its runs
@@ -665,87 +670,10 @@ FS_D bool walk_slice(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                      const int32_t* starts, uint64_t s, uint64_t nleaves, int lane, int32_t hk,
                      Cons& cons)
 {
-    if constexpr (Cons::PACKED) return walk_slice_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
-    if constexpr (Cons::LEX_PACKED)
+    if constexpr (Cons::ANY_ORDER)
+        return walk_slice_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
+    else
         return walk_slice_lex_packed(q, hs, dvh, starts, s, nleaves, lane, hk, cons);
-    RunPrefix rp;
-    int32_t b = warp_load_start(q, hs, starts, s, lane, rp);
-    const int np = q.P - 1;
-    const uint32_t hin = (uint32_t)hs[np];
-    const bool skip = q.sk_m[0] > 1 || q.sk_g[0] > 1;  // common-divisor skipping applies
-    uint64_t rem = nleaves;
-    for (;;) {
-        // the current run (prefix of levels 0..P-2) and its siblings
-        int32_t Rc = q.n, lpc = 0, ac = 0;
-        uint32_t hsib = 0, nsib = 1;
-        if (np > 0) {
-            Rc = __shfl_sync(FULL, rp.r, np - 1);
-            lpc = __shfl_sync(FULL, rp.l, np - 1);
-            ac = __shfl_sync(FULL, rp.a, np - 1);
-            hsib = (uint32_t)hs[np - 1];
-            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
-            if (nsib > 32) nsib = 32;
-        }
-        const int32_t Rj = (int32_t)((uint32_t)Rc - (uint32_t)lane * hsib);
-        for (uint32_t j = 0; j < nsib; j++) {
-            const int32_t R = __shfl_sync(FULL, Rj, (int)j);
-            const int32_t lp = lpc + (int32_t)j;
-            const uint32_t len = div32((uint32_t)R, q.dv_in) + 1;
-            const uint32_t left = len - (uint32_t)b;
-            const uint32_t nh = rem < (uint64_t)left ? (uint32_t)rem : left;
-            // the slice's leaves of this run are a = b .. b+nh-1; visit a = first
-            // + k ma, k < cnt (ma = 1: all of them)
-            uint32_t first = (uint32_t)b, cnt = nh, ma = 1;
-            if (Cons::SKIP && skip) skip_class(q, (uint32_t)R, (uint32_t)b, nh, first, cnt, ma);
-            if (cnt > 0) {
-                cons.run_begin(q, rp, lane, ac + (int32_t)j);
-                // wrap-around arithmetic: lanes past the run end get a
-                // meaningless r and are masked
-                const uint32_t astep = 32u * ma, step = astep * hin;
-                uint32_t a = first + (uint32_t)lane * ma;
-                uint32_t r = (uint32_t)R - a * hin;
-                const uint32_t full = cnt >> 5;  // steps with every lane in the run
-                uint32_t i = 0;
-                if (Cons::UNROLL > 1) {
-                    for (; i + Cons::UNROLL <= full; i += Cons::UNROLL) {
-#pragma unroll
-                        for (int u = 0; u < Cons::UNROLL; u++) {
-                            if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                            r -= step;
-                            a += astep;
-                        }
-                    }
-                }
-                for (; i < full; i++) {
-                    if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                    r -= step;
-                    a += astep;
-                }
-                if (cnt & 31)
-                    if (cons.chunk(q, lane, (uint32_t)lane < (cnt & 31), (int32_t)r, (int32_t)a, lp))
-                        return true;
-            }
-            rem -= nh;
-            if (rem == 0) return false;
-            b = 0;
-        }
-        // the last sibling becomes the current run; step to its lex successor
-        if (np == 0) {
-            cons.fault();  // the slice claims leaves past the last one
-            return false;
-        }
-        if (lane == np - 1) {
-            rp.a = ac + (int32_t)nsib - 1;
-            rp.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
-            rp.l = lpc + (int32_t)nsib - 1;
-        }
-        if (!warp_next_run(q, lane, hk, rp)) {
-            // the slice claims leaves past the last one: only a planner fault
-            // can cause this; flag it and end the walk rather than spin
-            cons.fault();
-            return false;
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
