@@ -421,6 +421,12 @@ fs_status fs_server_destroy(fs_server* s);
  * time individual kernels; off by default (no events recorded). */
 void fs_profile_enable(int on);
 
+/* Restricts the recording to the kernels timed under `name` (as
+ * fs_profile_read reports them, e.g. "pair_enum"); NULL or "" records every
+ * kernel again.  The string is copied.  Fewer events on the streams while a
+ * benchmark times a whole step. */
+void fs_profile_only(const char* name);
+
 /* Collects the timings recorded since the last read (waits for their events):
  * up to `max` entries, one per kernel name, in first-launch order.  names
  * (host, max * 32 chars, NUL-terminated entries), launches (host, max) = how

@@ -148,6 +148,7 @@ SIGNATURES = {
     "fs_server_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "fs_server_destroy": (ctypes.c_int, [_vp]),
     "fs_profile_enable": (None, [ctypes.c_int]),
+    "fs_profile_only": (None, [ctypes.c_char_p]),
     "fs_profile_read": (ctypes.c_int, [ctypes.c_char_p, _u64p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int]),
     "fs_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32,
@@ -531,6 +532,11 @@ class Server:
 def fs_profile_enable(on: bool = True) -> None:
     """Bracket every library kernel launch with CUDA events (for benchmarks)."""
     lib().fs_profile_enable(1 if on else 0)
+
+
+def fs_profile_only(name: str | None = None) -> None:
+    """Record only the kernels timed under `name` (None: every kernel)."""
+    lib().fs_profile_only(name.encode() if name else None)
 
 
 def fs_profile_read(max_entries: int = 64):

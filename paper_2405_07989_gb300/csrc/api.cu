@@ -119,13 +119,15 @@ struct ProfRec {
     int kernels;
 };
 bool g_prof = false;
+std::string g_prof_only;  // record only scopes of this name (empty: all)
 std::vector<ProfRec> g_prof_pending;
 
 struct ProfScope {
     ProfRec rec;
     cudaStream_t st;
     bool on;
-    ProfScope(const char* name, cudaStream_t s, int kernels) : st(s), on(g_prof && kernels > 0)
+    ProfScope(const char* name, cudaStream_t s, int kernels)
+        : st(s), on(g_prof && kernels > 0 && (g_prof_only.empty() || g_prof_only == name))
     {
         if (!on) return;
         rec.name = name;
@@ -1217,6 +1219,12 @@ void fs_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_prof = on != 0;
+}
+
+void fs_profile_only(const char* name)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prof_only = name ? name : "";
 }
 
 int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max)
