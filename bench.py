@@ -52,14 +52,30 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def kernel_source_sha() -> str:
-    h = hashlib.sha256()
+# the translation unit that defines each profiled kernel
+KERNEL_SOURCE = {"pair_enum": "enum_fixed.cu"}
+
+
+def kernel_source_sha(kernel: str = "pair_enum") -> str:
+    """Hash of the kernel's translation unit and every file it includes
+    (quoted #include lines, followed recursively): a change anywhere in the
+    code the kernel is compiled from changes it, host-only files do not."""
     csrc = os.path.join(ROOT, "paper_2405_07989_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    seen, todo = [], [os.path.join(csrc, KERNEL_SOURCE[kernel])]
+    while todo:
+        path = os.path.normpath(todo.pop())
+        if path in seen:
+            continue
+        seen.append(path)
+        with open(path) as f:
+            for line in f:
+                if line.startswith("#include \""):
+                    todo.append(os.path.join(os.path.dirname(path), line.split('"')[1]))
+    h = hashlib.sha256()
+    for path in sorted(seen):
+        with open(path, "rb") as f:
+            h.update(os.path.relpath(path, ROOT).encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -72,7 +88,7 @@ def recorded_traffic(kernel: str):
     with open(p) as f:
         rec = json.load(f)
     e = rec.get(kernel)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
