@@ -469,14 +469,21 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
     if (q.tab_xy)  // the write walk's pair tables, spread over the grid
         pair_tables_fill(q, nullptr, sc.X0, sc.YD, blockIdx.x * blockDim.x + tid,
                          gridDim.x * blockDim.x);
+    trailing_tables_block(q, 3, C + (size_t)(P - 1) * len, nullptr, nullptr, part64, part32);
+    // W_k and C_k are strided prefix sums of W_{k+1} and C_{k+1} with the same
+    // stride h_k: one pass for both where the chains are short
     for (int k = P - 2; k >= 0; k--) {
         const uint64_t* in = (k == P - 2) ? nullptr : Ws + (size_t)(k + 1) * len;
-        block_strided_prefix_sum(in, q.dv_in, Ws + (size_t)k * len, len, q.h[k], part64);
+        const uint64_t* cin = C + (size_t)(k + 1) * len;
+        const int h = q.h[k];
+        if (h < len && strided_by_warps(len, h)) {
+            warp_chains_scan2([&](int p) { return sps_in(in, p, q.dv_in); }, Ws + (size_t)k * len,
+                              [&](int p) { return cin[p]; }, C + (size_t)k * len, len, h);
+        } else {
+            block_strided_prefix_sum(in, q.dv_in, Ws + (size_t)k * len, len, h, part64);
+            block_strided_prefix_sum(cin, q.dv_in, C + (size_t)k * len, len, h, part64);
+        }
     }
-    trailing_tables_block(q, 3, C + (size_t)(P - 1) * len, nullptr, nullptr, part64, part32);
-    for (int k = P - 2; k >= 0; k--)
-        block_strided_prefix_sum(C + (size_t)(k + 1) * len, q.dv_in, C + (size_t)k * len, len,
-                                 q.h[k], part64);
     if (tid == 0) {
         const uint64_t L = total_leaves(q, Ws);
         uint64_t S = S_req;

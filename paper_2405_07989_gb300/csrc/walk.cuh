@@ -104,6 +104,54 @@ FS_D void warp_chains_scan(In in, T* out, int len, int s, Op op, T ident)
     __syncthreads();
 }
 
+// Two strided prefix sums with the same stride in one pass (same scheme as
+// warp_chains_scan): the two warp scans are independent, so each hides the
+// other's shuffle latency.  Caller guarantees s < len and strided_by_warps.
+template <class InA, class InB>
+FS_D void warp_chains_scan2(InA ina, uint64_t* outa, InB inb, uint64_t* outb, int len, int s)
+{
+    constexpr int EMAX = 8;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rho = threadIdx.x >> 5; rho < s; rho += nw) {
+        const int cl = (len - 1 - rho) / s + 1;
+        const int E = (cl + 31) >> 5;
+        const int t0 = lane * E;
+        uint64_t va[EMAX], vb[EMAX];
+#pragma unroll
+        for (int j = 0; j < EMAX; j++) {
+            const bool ok = j < E && t0 + j < cl;
+            const int p = rho + (t0 + j) * s;
+            va[j] = ok ? ina(p) : 0ull;
+            vb[j] = ok ? inb(p) : 0ull;
+        }
+#pragma unroll
+        for (int j = 1; j < EMAX; j++) {
+            va[j] += va[j - 1];
+            vb[j] += vb[j - 1];
+        }
+        uint64_t x = va[EMAX - 1], y = vb[EMAX - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(FULL, x, o);
+            const uint64_t v = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) {
+                x += u;
+                y += v;
+            }
+        }
+        uint64_t ea = __shfl_up_sync(FULL, x, 1), eb = __shfl_up_sync(FULL, y, 1);
+        if (lane == 0) ea = eb = 0;
+#pragma unroll
+        for (int j = 0; j < EMAX; j++)
+            if (j < E && t0 + j < cl) {
+                const int p = rho + (t0 + j) * s;
+                outa[p] = ea + va[j];
+                outb[p] = eb + vb[j];
+            }
+    }
+    __syncthreads();
+}
+
 FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint64_t* out, int len,
                                    int s, uint64_t* part)
 {
