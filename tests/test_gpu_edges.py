@@ -109,3 +109,50 @@ def test_empty_sets_every_method():
             assert fs.fs_enumerate(n, g, out, cap=4, cfg=cfg) == 0
             assert bool((out == -5).all())
             assert fs.fs_length_stats(n, g, None, cfg) == (0, 0, 0)
+
+
+def _lattice_reference(n, g):
+    """For g = (H, 1, A, B): |Z| and the length range by direct summation over
+    a_0 and x (a_1 takes up whatever x A + y B leaves of n - a_0 H)."""
+    H, _, A, B = g
+    total, lo, hi = 0, None, None
+    for a0 in range(n // H + 1):
+        R = n - a0 * H
+        for x in range(R // A + 1):
+            ymax = (R - x * A) // B
+            total += ymax + 1
+            shortest = a0 + (R - x * A - ymax * B) + x + ymax  # a_1 smallest
+            lo = shortest if lo is None else min(lo, shortest)
+        hi = max(hi or 0, a0 + R)  # x = y = 0: a_1 = R
+    return total, lo, hi
+
+
+def test_sibling_runs_with_more_than_two_to_the_31_leaves():
+    """Runs of up to 10^9 leaves each (generator 1 innermost, 8 sibling runs):
+    the walks take a sibling group's runs only while their leaves stay below
+    2^31 and continue with the next group.  The pair (200000, 300000) has
+    common divisor 10^5, so the length walk (which skips) visits one leaf in
+    10^5 and can take the whole set as a single slice, which crosses that cap
+    twice.  Count and length range against a direct summation; the
+    ordered rows are valid factorizations, strictly lex-ascending, and as many
+    as the count: that is Z, in order.  (The leaf-count table of this query
+    takes 7.5 GiB, under the library's 8 GiB limit.)"""
+    g = (1 << 27, 1, 200000, 300000)
+    n = 10**9
+    Z, lo, hi = _lattice_reference(n, g)
+    assert (Z, lo, hi) == (25066630, 3334, 10**9)
+    for keep in (True, False):
+        assert fs.fs_count(n, g, fs.make_config(keep_order=keep)) == Z, keep
+    for keep, slices in ((True, 0), (True, 1), (False, 0)):
+        cfg = fs.make_config(keep_order=keep, slices=slices)
+        assert fs.fs_length_stats(n, g, None, cfg) == (Z, lo, hi), (keep, slices)
+    out = torch.full((Z, 4), -1, dtype=torch.int32, device="cuda")
+    gt = torch.tensor(g, dtype=torch.int64, device="cuda")
+    assert fs.fs_enumerate(n, g, out, cap=Z, cfg=fs.make_config(keep_order=True)) == Z
+    assert bool(((out.long() * gt).sum(1) == n).all())
+    diff = out[1:].long() - out[:-1].long()
+    nz = diff != 0
+    first = nz.to(torch.int32).argmax(1, keepdim=True)
+    assert bool(nz.any(1).all()) and bool((diff.gather(1, first) > 0).all())
+    del out, diff, nz, first
+    torch.cuda.empty_cache()
