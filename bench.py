@@ -56,10 +56,36 @@ def measured_peaks():
 KERNEL_SOURCE = {"pair_enum": "enum_fixed.cu"}
 
 
+def strip_c_comments(src: str) -> str:
+    """C/C++ source without comments (string and character literals kept) and
+    with every run of whitespace reduced to one space."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_sha(kernel: str = "pair_enum") -> str:
     """Hash of the kernel's translation unit and every file it includes
-    (quoted #include lines, followed recursively): a change anywhere in the
-    code the kernel is compiled from changes it, host-only files do not."""
+    (quoted #include lines, followed recursively), comments and whitespace
+    aside: a change anywhere in the code the kernel is compiled from changes
+    it; host-only files and comments do not."""
     csrc = os.path.join(ROOT, "paper_2405_07989_gb300", "csrc")
     seen, todo = [], [os.path.join(csrc, KERNEL_SOURCE[kernel])]
     while todo:
@@ -73,9 +99,9 @@ def kernel_source_sha(kernel: str = "pair_enum") -> str:
                     todo.append(os.path.join(os.path.dirname(path), line.split('"')[1]))
     h = hashlib.sha256()
     for path in sorted(seen):
-        with open(path, "rb") as f:
+        with open(path) as f:
             h.update(os.path.relpath(path, ROOT).encode())
-            h.update(f.read())
+            h.update(strip_c_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -54,8 +54,8 @@ typedef enum fs_status {
     FS_OK = 0,
     FS_E_INVAL = 1,     /* bad argument: d out of range, zero generator, n < 0, NULL pointer */
     FS_E_OVERFLOW = 2,  /* n + max g >= 2^31, int16 output that cannot hold a coordinate,
-                           a planner table that would exceed its size limit, or a query
-                           whose count may reach 2^63: the bound
+                           planner leaf-count tables ((P-1) (n+1) uint64, P = max(d,3) - 2)
+                           above 8 GiB, or a query whose count may reach 2^63: the bound
                            (n + sum g)^(d-1) / ((d-1)! prod g) over the d-1 largest
                            generators is checked before any work */
     FS_E_CAPACITY = 3,  /* enumerate: more factorizations than `cap` */
