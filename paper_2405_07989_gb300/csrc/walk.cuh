@@ -6,8 +6,9 @@
 // bounds are clean prefixes (leaf, 0, 0), so each worker's stream starts at a
 // state that satisfies the hypothesis of Thm 3.2, cf. Remark 4.2).  A warp
 // takes one slice at a time, finds the slice's first leaf from the exact leaf
-// counts W (the planner), and then walks the slice's leaves in lex order, 32
-// leaves per step: lane l takes the l-th next leaf.
+// counts W (the planner), and then walks the slice's leaves 32 per step, a
+// group of sibling runs at a time: in lex order for enumerate, full steps run
+// by run and the runs' remainders packed for the order-free consumers.
 #pragma once
 
 #include <cuda_runtime.h>
