@@ -488,6 +488,17 @@ def run_gpu(args):
 COUNT_OPS_PER_LEAF = 8
 
 
+def visited_leaves(leaves: int, gens) -> int:
+    """The leaves the PAIR walk (descending order) resolves: those whose
+    residual is a multiple of G = gcd of the last two generators, since only
+    they can complete (Sec. 3.2.4).  With the innermost walk generator h, a
+    run's residuals step by h, so a fraction gcd(h, G) / G of a run's leaves
+    qualifies and a fraction 1 / gcd(h, G) of the runs has any: leaves / G
+    in all, up to a leaf per run."""
+    w = sorted(gens, reverse=True)
+    return leaves // math.gcd(w[-1], w[-2]) if len(w) >= 3 else leaves
+
+
 def heavy_count_extras(fs, workloads, dev):
     """Count and length statistics of the count-only heavy query (8 generators
     from seed 0, n = 40000, 7.66e12 factorizations), event-timed, with the
@@ -520,7 +531,8 @@ def heavy_count_extras(fs, workloads, dev):
     Z3, ms3, walk3, prof3 = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count")
     Z4, ms4, walk4, prof4 = timed_count(None, "quad_count")
     assert Z3 == Z and Z4 == Z
-    achieved = leaves * COUNT_OPS_PER_LEAF / (walk_ms / 1000.0)
+    visited = visited_leaves(leaves, g)
+    achieved = visited * COUNT_OPS_PER_LEAF / (walk_ms / 1000.0)
     hist = torch.zeros(n // min(g) + 1, dtype=torch.int64, device=dev)
     t0 = time.perf_counter()
     cnt, mn, mx = fs.fs_length_stats(n, g, hist)
@@ -538,13 +550,16 @@ def heavy_count_extras(fs, workloads, dev):
         z3, ms3s, _, _ = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count", ns, gs)
         z4, ms4s, _, _ = timed_count(None, "quad_count", ns, gs)
         assert z3 == zs and z4 == zs
+        vs = visited_leaves(lv, gs)
         seeds[str(seed)] = {"gens": list(gs), "n": ns, "factorizations": zs, "leaves": lv,
+                            "leaves_visited": vs,
                             "count_ms": mss, "count_leaves_per_s": lv / (wms / 1000.0),
-                            "count_roofline_frac": lv * COUNT_OPS_PER_LEAF / (wms / 1000.0) / rates["add"],
+                            "count_roofline_frac": vs * COUNT_OPS_PER_LEAF / (wms / 1000.0) / rates["add"],
                             "count_triple_ms": ms3s, "count_quad_ms": ms4s}
     return {
         "workload": f"count-only heavy query g={tuple(g)}, n={n}",
-        "factorizations": Z, "leaves": leaves, "count_ms": ms, "count_walk_ms": walk_ms,
+        "factorizations": Z, "leaves": leaves, "leaves_visited": visited,
+        "count_ms": ms, "count_walk_ms": walk_ms,
         "count_factorizations_per_s": Z / (ms / 1000.0), "count_leaves_per_s": leaves / (walk_ms / 1000.0),
         "count_triple_ms": ms3, "count_triple_walk_ms": walk3,
         "count_triple_factorizations_per_s": Z / (ms3 / 1000.0),
@@ -554,7 +569,8 @@ def heavy_count_extras(fs, workloads, dev):
         "count_quad_breakdown_ms": {k: v[1] for k, v in prof4.items()},
         "count_roofline": {"bound": "alu", "achieved": achieved, "peak": rates["add"],
                            "unit": "int32 lane-ops/s", "frac": achieved / rates["add"],
-                           "ops_per_leaf": COUNT_OPS_PER_LEAF, "peak_source": "probed add rate"},
+                           "ops_per_leaf": COUNT_OPS_PER_LEAF, "per": "visited leaf",
+                           "peak_source": "probed add rate"},
         "int_rates": rates,
         "length_stats_s": len_s, "length_min_max": [mn, mx],
         "length_factorizations_per_s": Z / len_s,

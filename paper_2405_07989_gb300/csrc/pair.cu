@@ -20,7 +20,7 @@ struct CountCons {
     uint64_t total;  // this lane, all slices
     uint64_t* ctr;
     static constexpr int UNROLL = 4;
-    static constexpr bool SKIP = false;
+    static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
