@@ -24,11 +24,13 @@
  *                           prod 1/(1-y x^{g_i}).
  *   oracle_minmax_dp        min / max of sum a_i by unbounded-knapsack recurrences.
  *
- * Readings of the paper taken here (each also listed in the design notes):
+ * Readings of the paper taken here:
  *   - decrementAndSolve divides by g_{i+1}; the "/g_1" in Sec. 3.2.2 is a typo.
- *   - step 2 of Algorithm 3.1 scans j = 1..d-1 (the text excludes index d).
- *   - phi in step 6 is taken over the whole candidate after steps 4-5, where the
- *     coordinates right of i are zero.
+ *   - the pivot of nextCandidate (Algorithm 3.1) is searched among the first
+ *     d-1 coordinates only: the text excludes the final one, although the
+ *     printed loop bound reads "dim".
+ *   - the residual decrementAndSolve divides is n minus phi of the candidate
+ *     after the pivot is lowered and everything right of it cleared.
  *   - bounds are half-open: a stream for the slice [lo, hi) starts from hi
  *     (not emitted) or from the first candidate when hi is +infinity, and ends
  *     as soon as a candidate is lex-smaller than lo.  The paper's end test
@@ -81,41 +83,45 @@ static void first_candidate(int64_t n, const int64_t* g, int d, int64_t* a, int*
 }
 
 /*
- * nextCandidate (Algorithm 3.1), in place.  Indices in the comments are the
- * paper's 1-based ones; a[k-1] holds a_k.  `lo` is the inclusive lower bound of
- * the slice (NULL for the whole stream).  Returns 0 at endOfStream, else 1, and
- * sets *was_valid for the candidate left in a.
+ * nextCandidate (Sec. 3.2.2, Algorithm 3.1), in place; a[k] holds the
+ * coordinate of generator k (0-based here, 1-based in the paper).
+ *
+ * The stream runs through N^d in decreasing lex order, but only over the
+ * candidates: vectors whose last nonzero coordinate is the least value that
+ * brings phi up to at least n.  The candidate after a keeps the longest prefix
+ * it can: the pivot is the last nonzero coordinate among the first d-1; it
+ * drops by one, everything right of it is cleared, and the coordinate just
+ * right of it becomes ceil(rest / g), rest = n - phi of what is left and g its
+ * generator (decrementAndSolve).  The new candidate is a factorization exactly
+ * when that division is exact.  Thm 3.2: no factorization between a and it is
+ * skipped.  With no pivot (a = (0,..,0,x)) nothing is left below and the
+ * stream ends; it also ends once a candidate falls below `lo`, the slice's
+ * inclusive lower bound (NULL for none).
+ *
+ * rest >= 1 always: a's prefix up to the pivot was itself reached from below
+ * n by a least-value solve (or is the first candidate), so lowering the pivot
+ * puts phi strictly below n.
+ *
+ * Returns 0 at the end of the stream, else 1 with *was_valid set for the
+ * candidate left in a.
  */
 static int next_candidate(int64_t n, const int64_t* g, int d, int64_t* a,
                           const int64_t* lo, int* was_valid)
 {
-    /* step 2: i = the rightmost index in 1..d-1 with a_i > 0 (0 if none) */
-    int i = 0;
-    int last = (oracle_mutation == 2) ? d : d - 1; /* mutation: include index d */
-    for (int j = 1; j <= last; j++)
-        if (a[j - 1] > 0) i = j;
-    /* step 3: the previous candidate was (0,...,0,x): end of stream */
-    if (i == 0) return 0;
-    if (i == d) return 0; /* only reachable under mutation 2: nothing right of d */
-    /* step 4: reset the final coordinate */
-    a[d - 1] = 0;
-    /* step 5: decrement a_i (first step of decrementAndSolve) */
-    a[i - 1] -= 1;
-    /* step 6: p = n - phi(a), what is left to factor by g_{i+1} */
-    int64_t p = n - phi(a, g, d);
-    /* steps 7-10: m = ceil(p / g_{i+1}); valid iff the division is exact */
-    int64_t gi1 = (oracle_mutation == 1) ? g[0] : g[i]; /* mutation: the "/g_1" typo */
-    int64_t m = p / gi1;
-    int64_t r = p - m * gi1;
-    *was_valid = 1;
-    if (r != 0) {
-        m += 1;
-        *was_valid = 0;
-    }
-    if (oracle_mutation == 5 && r == 0 && i + 1 < d) *was_valid = 0; /* mutation: drop exact inner solves */
-    /* step 11 */
-    a[i] = m;
-    /* step 12: end of the slice once the candidate falls below its lower bound */
+    int scan = (oracle_mutation == 2) ? d : d - 1; /* mutation: the pivot may be the last */
+    int piv = -1;
+    for (int k = 0; k < scan; k++)
+        if (a[k] > 0) piv = k;
+    if (piv < 0 || piv == d - 1) return 0; /* piv == d-1 only under mutation 2 */
+    a[piv] -= 1;
+    for (int k = piv + 1; k < d; k++) a[k] = 0;
+    int64_t rest = n - phi(a, g, d);
+    int64_t gn = (oracle_mutation == 1) ? g[0] : g[piv + 1]; /* mutation: the "/g_1" typo */
+    int64_t q = rest / gn;
+    int exact = (q * gn == rest);
+    a[piv + 1] = exact ? q : q + 1;
+    *was_valid = exact;
+    if (oracle_mutation == 5 && exact && piv + 2 < d) *was_valid = 0; /* mutation: drop exact inner solves */
     if (lo && lex_cmp(a, lo, d) < 0) return 0;
     return 1;
 }

@@ -1,5 +1,5 @@
-// The PLAIN method: Algorithm 3.1 (nextCandidate) exactly as the paper gives
-// it, one bounded stream per GPU thread with the whole state in registers
+// The PLAIN method: the paper's successor (nextCandidate, Sec. 3.2.2) with no
+// shortcut, one bounded stream per GPU thread with the whole state in registers
 // (Sec. 3.1.2, Sec. 5).  A thread pops a slice [lo, hi) from the device queue,
 // starts at hi (or at the first candidate of Sec. 3.2.1 for the last slice),
 // and steps nextCandidate until the candidate drops below lo, consuming the
@@ -28,46 +28,43 @@ FS_D void load_start_thread(const QueryConst& q, const int32_t* starts, uint64_t
         if (k == q.P - 1) v[k] = st[START_W - 1];
 }
 
-// One nextCandidate step (Algorithm 3.1, steps 2-12).  Returns false at the
-// end of the slice's stream; sets `valid` (wasValid) otherwise.
+// The successor of a candidate in the lex-decreasing stream (nextCandidate,
+// Sec. 3.2.2): the pivot is the last nonzero coordinate before the final one;
+// it drops by one, the coordinates right of it are cleared, and the one just
+// right of it takes the least value that brings phi up to at least n (the
+// ceiling of the residual over its generator; the residual is at least 1, as
+// the pivot's prefix was reached from below n).  The new candidate is a
+// factorization exactly when that division is exact, and by Thm 3.2 none is
+// skipped.  Returns false when there is no pivot or the candidate falls below
+// the slice's lower bound `lo`; otherwise sets `valid` (wasValid).
 template <int MAXD>
 FS_D bool next_candidate(const QueryConst& q, const SmemQP& sq, int32_t (&a)[MAXD],
                          const int32_t (&lo)[MAXD], bool& valid)
 {
     const int D = q.D;
-    // step 2: the rightmost index i < D-1 (0-based) with a_i > 0
-    int i = -1;
+    int piv = -1;
 #pragma unroll
     for (int k = 0; k < MAXD - 1; k++)
-        if (k < D - 1 && a[k] > 0) i = k;
-    // step 3: the previous candidate was (0, .., 0, x)
-    if (i < 0) return false;
-    // step 4: reset the final coordinate; step 5: decrement a_i
-#pragma unroll
-    for (int k = 0; k < MAXD; k++) {
-        if (k == D - 1) a[k] = 0;
-        if (k == i) a[k] -= 1;
-    }
-    // step 6: p = n - phi(a)
+        if (k < D - 1 && a[k] > 0) piv = k;
+    if (piv < 0) return false;
+    // lower the pivot, clear the rest (only the final coordinate can be
+    // nonzero right of the pivot), and sum phi of what is left
     int64_t phi = 0;
 #pragma unroll
-    for (int k = 0; k < MAXD; k++)
+    for (int k = 0; k < MAXD; k++) {
+        if (k == piv) a[k] -= 1;
+        if (k > piv) a[k] = 0;
         if (k < D) phi += (int64_t)a[k] * sq.h[k];
-    const int32_t p = q.n - (int32_t)phi;
-    // steps 7-10: m = ceil(p / g_{i+1}), valid iff exact
-    const int32_t hn = sq.h[i + 1];
-    int32_t m = (int32_t)div32((uint32_t)p, sq.dvh[i + 1]);
-    const int32_t rr = p - m * hn;
-    valid = true;
-    if (rr != 0) {
-        m += 1;
-        valid = false;
     }
-    // step 11
+    const int32_t rest = q.n - (int32_t)phi;
+    const int32_t hn = sq.h[piv + 1];
+    int32_t m = (int32_t)div32((uint32_t)rest, sq.dvh[piv + 1]);
+    valid = m * hn == rest;
+    if (!valid) m += 1;
 #pragma unroll
     for (int k = 0; k < MAXD; k++)
-        if (k == i + 1) a[k] = m;
-    // step 12: end of the slice when the candidate is below its lower bound
+        if (k == piv + 1) a[k] = m;
+    // lex comparison with the slice's lower bound
     int cmp = 0;
 #pragma unroll
     for (int k = 0; k < MAXD; k++)
