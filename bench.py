@@ -44,6 +44,12 @@ FALLBACK_HBM_GBS = 6800.0
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+def bench_config(Z: int, row_bytes: int) -> dict:
+    """The `config` object both arms print for the bench workload."""
+    return {"workload": WORKLOAD, "factorizations_per_step": Z, "output_bytes": Z * row_bytes,
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -293,7 +299,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "factorizations/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": bench_config(tot, 4 * len(g)),
         "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
                          "kind": "oracle",
                          "sample": f"whole query per step: oracle bounded streams (Algorithm 3.1,"
@@ -469,8 +475,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "factorizations_per_step": Z,
-                       "output_bytes": alg_bytes, "l2": "flushed between steps (256 MB write)"},
+            "config": bench_config(Z, row_bytes),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "gpu_launches_per_step": launches_per_step,
             "clocks": clk, "breakdown": breakdown, "host_enqueue_ms_per_step": host_ms,
@@ -769,7 +774,8 @@ def run_profile_case(args):
     "enum": the single-large-query generators at a smaller n (output still
     larger than L2); "count" / "count_triple" / "count_quad": the heavy
     count-only query's generators at --profile-n through the PAIR walk or the
-    trailing-three / trailing-four tables; "batch": the first --profile-n
+    trailing-three / trailing-four tables; "lengths": the same generators'
+    count, length range and histogram (PAIR walk); "batch": the first --profile-n
     queries of the batched workload, count mode."""
     import torch
     import paper_2405_07989_gb300 as fs
@@ -783,11 +789,20 @@ def run_profile_case(args):
         print(json.dumps({"profile_case": {"queries": len(qs), "calls": args.steps,
                                            "factorizations": sum(r[0] for r in res)}}))
         return 0
+    walk = {"auto": fs.WALK_AUTO, "packed": fs.WALK_PACKED, "lanes": fs.WALK_LANES}[args.profile_walk]
+    if args.profile_case == "lengths":
+        n, g = workloads.config3(0, n=args.profile_n)
+        hist = torch.zeros(n // min(g) + 1, dtype=torch.int64, device="cuda")
+        for _ in range(args.steps):
+            res = fs.fs_length_stats(n, g, hist, fs.make_config(walk=walk))
+        print(json.dumps({"profile_case": {"n": n, "gens": list(g), "count": res[0],
+                                           "min_max": list(res[1:]), "calls": args.steps}}))
+        return 0
     if args.profile_case in ("count", "count_triple", "count_quad"):
         n, g = workloads.config3(0, n=args.profile_n)
         dc = torch.zeros(1, dtype=torch.int64, device="cuda")
         cfg = fs.make_config(method={"count": fs.METHOD_PAIR, "count_triple": fs.METHOD_TRIPLE,
-                                     "count_quad": fs.METHOD_QUAD}[args.profile_case])
+                                     "count_quad": fs.METHOD_QUAD}[args.profile_case], walk=walk)
         for _ in range(args.steps):
             fs.fs_count_async(n, g, dc, cfg)
         torch.cuda.synchronize()
@@ -819,10 +834,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the heavy count-only query measurements")
-    ap.add_argument("--profile-case", choices=["enum", "count", "count_triple", "count_quad", "batch"],
+    ap.add_argument("--profile-case",
+                    choices=["enum", "count", "count_triple", "count_quad", "lengths", "batch"],
                     default=None,
                     help="run only a small case of the same kernels (for ncu)")
     ap.add_argument("--profile-n", type=int, default=2000)
+    ap.add_argument("--profile-walk", choices=["auto", "packed", "lanes"], default="auto",
+                    help="profile cases: how the order-free walks take a sibling group")
     ap.add_argument("--serve-rate", type=float, default=1000.0,
                     help="serving extras: Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=2000)

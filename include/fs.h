@@ -99,7 +99,18 @@ typedef struct fs_config {
     int64_t slices;        /* number of lexicographic slices [lo,hi) (Sec. 4); 0 = auto */
     int32_t block_threads; /* threads per block; 0 = auto */
     int32_t blocks_per_sm; /* resident blocks per SM for the persistent grid; 0 = auto */
+    int32_t walk;          /* fs_walk: how the order-free consumers (count, length
+                              statistics, predicate, trailing-table walks) take the leaves
+                              of a group of sibling runs; the results are the same */
+    int32_t reserved;      /* must be 0 */
 } fs_config;
+
+/* fs_config.walk.  PACKED: each run's full 32-leaf steps with the warp on one
+ * run, then the runs' remainders packed into shared steps.  LANES: lane j walks
+ * sibling run j on its own, the warp stepping until the longest run is done.
+ * AUTO (0): per group of sibling runs, whichever costs fewer issue slots by
+ * the walk's own estimate. */
+typedef enum { FS_WALK_AUTO = 0, FS_WALK_PACKED = 1, FS_WALK_LANES = 2 } fs_walk;
 
 /* Fills *cfg with the defaults (all zero = automatic). */
 void fs_config_default(fs_config* cfg);
@@ -463,10 +474,21 @@ int fs_profile_read(char* names, uint64_t* launches, double* total_ms, int max);
  * - every call on a device shares the one array and each call re-zeroes the
  *   counters it needs; calls whose work overlaps on the GPU (different
  *   streams, no ordering between them) race on the array and give wrong
- *   results: order them on one stream or with events. */
+ *   results: order them on one stream or with events;
+ * - the looked-up address is kept per device for the life of the process and
+ *   forgotten when a call on that device meets a CUDA error; after
+ *   cudaDeviceReset on a device, no call of this library may be made on it
+ *   again in this process (its cached arenas and addresses belong to the
+ *   destroyed context). */
 #define FS_NOALLOC_SCRATCH_BYTES (4u << 20)
 fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, uint64_t* dev_count,
                            void* stream);
+
+/* Number of successful device allocations (cudaMalloc) and pinned host
+ * allocations (cudaMallocHost) this library has made in this process, on all
+ * devices: lets a caller check that a call allocated nothing (for instance
+ * fs_count_noalloc).  Null pointers are skipped.  Host-only, never fails. */
+void fs_alloc_counts(uint64_t* device_allocs, uint64_t* pinned_host_allocs);
 
 /* --- integer throughput probe ------------------------------------------- */
 

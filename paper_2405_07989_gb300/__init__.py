@@ -20,6 +20,7 @@ MAX_D = 16
 FS_OK, FS_E_INVAL, FS_E_OVERFLOW, FS_E_CAPACITY = 0, 1, 2, 3
 FS_E_NOMEM, FS_E_CUDA, FS_E_TIMEOUT, FS_E_NOTIMPL = 4, 5, 6, 7
 METHOD_AUTO, METHOD_PLAIN, METHOD_PAIR, METHOD_TRIPLE, METHOD_QUAD = 0, 1, 2, 3, 4
+WALK_AUTO, WALK_PACKED, WALK_LANES = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -34,7 +35,8 @@ class FsError(RuntimeError):
 class fs_config(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("keep_order", ctypes.c_int32),
                 ("slices", ctypes.c_int64), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("walk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class fs_len_summary(ctypes.Structure):
@@ -123,6 +125,7 @@ SIGNATURES = {
     "fs_slice_counts": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
                                        ctypes.c_int64, _u64p, _vp]),
     "fs_count_noalloc": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _vp, _vp]),
+    "fs_alloc_counts": (None, [_u64p, _u64p]),
     "fs_batch_create": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int, _cfgp,
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "fs_batch_launch": (ctypes.c_int, [_vp, _vp]),
@@ -203,9 +206,9 @@ def _stream(stream):
 
 
 def make_config(method: int = METHOD_AUTO, keep_order: bool = False, slices: int = 0,
-                block_threads: int = 0, blocks_per_sm: int = 0) -> fs_config:
+                block_threads: int = 0, blocks_per_sm: int = 0, walk: int = 0) -> fs_config:
     return fs_config(int(method), int(bool(keep_order)), int(slices), int(block_threads),
-                     int(blocks_per_sm))
+                     int(blocks_per_sm), int(walk), 0)
 
 
 def _cfgp_of(cfg):
@@ -391,6 +394,14 @@ def fs_count_noalloc(n: int, gens, dev_count, stream=None) -> None:
     |Z| lands in dev_count[0] (a CUDA 64-bit tensor)."""
     g, d = _gens(gens)
     _check(lib().fs_count_noalloc(int(n), g, d, _ptr(dev_count), _stream(stream)))
+
+
+def fs_alloc_counts():
+    """(device allocations, pinned host allocations) the library has made in
+    this process."""
+    dv, hv = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    lib().fs_alloc_counts(ctypes.byref(dv), ctypes.byref(hv))
+    return int(dv.value), int(hv.value)
 
 
 def _queries(queries):

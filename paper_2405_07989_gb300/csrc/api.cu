@@ -71,7 +71,7 @@ fs_status get_dev(DevState** out)
     if (ds.sms == 0) {
         e = cudaDeviceGetAttribute(&ds.sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        e = cudaMallocHost((void**)&ds.pinned, 4096);
+        e = host_alloc((void**)&ds.pinned, 4096);
         if (e != cudaSuccess) {
             ds.sms = 0;
             return fail(FS_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
@@ -99,7 +99,7 @@ fs_status ensure_arena(DevState* ds, cudaStream_t st, size_t bytes, void** out)
     }
     size_t want = std::max(bytes, (size_t)16 << 20);
     want = (want + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
-    cudaError_t e = cudaMalloc(&a.p, want);
+    cudaError_t e = dev_alloc(&a.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         a.p = nullptr;
@@ -209,9 +209,13 @@ fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& c
                         "the factorization count may exceed 2^63 (bound 2^%.1f): not representable",
                         (double)(lg / logl(2.0L)));
     }
+    if (cfg.walk < FS_WALK_AUTO || cfg.walk > FS_WALK_LANES)
+        return fail(FS_E_INVAL, "walk = %d: not an fs_walk", cfg.walk);
+    if (cfg.reserved != 0) return fail(FS_E_INVAL, "fs_config.reserved = %d: must be 0", cfg.reserved);
     QueryConst& q = Q.q;
     memset(&q, 0, sizeof q);
     q.n = (int32_t)n;
+    q.walk = cfg.walk;
     q.d = d;
     q.D = std::max(d, 3);
     q.P = q.D - 2;
@@ -968,7 +972,7 @@ fs_status stage_ready(DevState* ds, size_t bytes)
         ds->stage = nullptr;
         ds->stage_size = 0;
     }
-    cudaError_t e = cudaMalloc(&ds->stage, bytes);
+    cudaError_t e = dev_alloc(&ds->stage, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ds->stage = nullptr;
@@ -1004,7 +1008,7 @@ fs_status fs_cursor_create(int64_t n, const uint32_t* gens, int d, const fs_conf
     if (s == FS_OK && c.method != FS_METHOD_PAIR)
         s = fail(FS_E_NOTIMPL, "a cursor walks the PAIR method (method %d asked)", c.cfg.method);
     if (s == FS_OK) {
-        cudaError_t e = cudaMalloc(&k->mem, c.L.total);
+        cudaError_t e = dev_alloc(&k->mem, c.L.total);
         if (e != cudaSuccess) {
             cudaGetLastError();
             k->mem = nullptr;
@@ -1328,6 +1332,7 @@ uint64_t batch_plan_host(const fs_query* queries, int nq, int mode, const fs_con
         return o;
     };
     fs_config walk_cfg = cfg_or_default(nullptr);  // descending walk order
+    walk_cfg.walk = cc.walk;                         // the caller's sibling-group mode
     for (int i = 0; i < nq; i++) {
         BatchQ& B = out[i];
         memset(&B, 0, sizeof B);
@@ -1411,10 +1416,10 @@ fs_status fs_batch_reserve(int max_queries, uint64_t table_bytes, int mode, cons
     const size_t off_st = al(off_ctr + BCTR_N * 8);
     const size_t off_ar = al(off_st + (size_t)b->bd.items_cap * START_W * 4);
     const size_t total = al(off_ar + table_bytes);
-    e = cudaMalloc(&b->mem, total);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->hq, sizeof(BatchQ) * (size_t)max_queries);
+    e = dev_alloc(&b->mem, total);
+    if (e == cudaSuccess) e = host_alloc((void**)&b->hq, sizeof(BatchQ) * (size_t)max_queries);
     if (e == cudaSuccess)
-        e = cudaMallocHost((void**)&b->hres, sizeof(BatchRes) * (size_t)max_queries + BCTR_N * 8);
+        e = host_alloc((void**)&b->hres, sizeof(BatchRes) * (size_t)max_queries + BCTR_N * 8);
     if (e != cudaSuccess) {
         cudaGetLastError();
         batch_free(b);
@@ -1680,7 +1685,10 @@ extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, ui
     }
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (e != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
     LaunchCfg lc;
     s = geometry(q, cfg, OP_COUNT, FS_METHOD_PAIR, 4, sms, lc);
     if (s != FS_OK) return s;
@@ -1695,15 +1703,27 @@ extern "C" fs_status fs_count_noalloc(int64_t n, const uint32_t* gens, int d, ui
     sc.starts = (int32_t*)(base + off_st);
     cudaStream_t st = (cudaStream_t)stream;
     // the counters (slice queue head, total) must start at zero on every call
+    const char* what = "cudaMemsetAsync";
     e = cudaMemsetAsync(sc.ctr, 0, CTR_N * 8, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_precompute(q, sc, st);
-    if (e != cudaSuccess) return cuda_fail(e, "precompute launch");
-    e = launch_plan(q, sc, lc.S, lc.auto_s, lc.min_leaves, st);
-    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
-    e = launch_pair(q, sc, OP_COUNT, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, st);
-    if (e != cudaSuccess) return cuda_fail(e, "count launch");
-    e = launch_copy_u64(sc.ctr + CTR_COUNT, dev_count, st);
-    if (e != cudaSuccess) return cuda_fail(e, "copy launch");
+    if (e == cudaSuccess) {
+        what = "precompute launch";
+        e = launch_precompute(q, sc, st);
+    }
+    if (e == cudaSuccess) {
+        what = "planner launch";
+        e = launch_plan(q, sc, lc.S, lc.auto_s, lc.min_leaves, st);
+    }
+    if (e == cudaSuccess) {
+        what = "count launch";
+        e = launch_pair(q, sc, OP_COUNT, lc, CTR_QUEUE, nullptr, nullptr, 0, 4, st);
+    }
+    if (e == cudaSuccess) {
+        what = "copy launch";
+        e = launch_copy_u64(sc.ctr + CTR_COUNT, dev_count, st);
+    }
+    if (e != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;  // looked up again by the next call
+        return cuda_fail(e, what);
+    }
     return FS_OK;
 }

@@ -165,6 +165,8 @@ struct BatchCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = false;
     static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = MODE ? 24 : 12;
+    static constexpr bool R_INDEXED = false;
     FS_D void fault()
     {
         if ((threadIdx.x & 31) == 0) atomicOr((unsigned long long*)&ctr[BCTR_ERR], 1ull);

@@ -99,7 +99,7 @@ struct QueryConst {
     // (reduce_to_trailing moves them to 0).  sk_g = sk_m = 1: nothing skipped.
     int32_t sk_g[3], sk_m[3], sk_inv[3];
     Div32 dv_skg[3], dv_skm[3];
-    int32_t pad0;
+    int32_t walk;         // fs_walk: how the order-free walks take a sibling group
 };
 
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <tuple>
 
@@ -71,4 +72,27 @@ cudaError_t sm_count_cached(int* sms)
     return e;
 }
 
+// Allocation counters (fs_alloc_counts).
+static std::atomic<uint64_t> g_dev_allocs{0}, g_host_allocs{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes)
+{
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+cudaError_t host_alloc(void** p, size_t bytes)
+{
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) g_host_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
 }  // namespace fsi
+
+extern "C" void fs_alloc_counts(uint64_t* device_allocs, uint64_t* pinned_host_allocs)
+{
+    if (device_allocs) *device_allocs = fsi::g_dev_allocs.load(std::memory_order_relaxed);
+    if (pinned_host_allocs) *pinned_host_allocs = fsi::g_host_allocs.load(std::memory_order_relaxed);
+}

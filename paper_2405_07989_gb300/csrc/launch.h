@@ -14,6 +14,11 @@ cudaError_t occupancy_cached(const void* kern, int threads, int smem, int* nb);
 cudaError_t smem_optin(const void* kern, int smem);
 cudaError_t sm_count_cached(int* sms);
 
+// Every device and pinned-host allocation of the library goes through these
+// (hostcache.cu), which count the successful ones (fs_alloc_counts).
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
+
 
 enum Op { OP_COUNT = 0, OP_SLICES = 1, OP_LEN = 2, OP_ANY = 3, OP_ENUM = 4 };
 

@@ -12,9 +12,15 @@ namespace fsi {
 // ===========================================================================
 // count
 // ===========================================================================
+// The count of a leaf with residual r = qq lcm + w is qq + E[w], E[w] in
+// {0, 1} for every w the walk visits (its residual is a multiple of G by
+// common-divisor skipping; E[w] = -1 marks the other classes).  The table path
+// keeps E as a bitmask, one 32-bit word per 32 classes, with every word
+// repeated 32 times so that lane l reads its own copy at bank l: the lanes'
+// lookups at scattered w never meet in a bank (4 lcm bytes, 64 KB at most).
 template <bool TAB, bool PER_SLICE>
 struct CountCons {
-    const int8_t* E;
+    const uint32_t* Eb;  // TAB: the replicated bitmask
     uint64_t* slice_cnt;
     uint64_t acc;    // this lane, current slice
     uint64_t total;  // this lane, all slices
@@ -22,6 +28,8 @@ struct CountCons {
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = 11;
+    static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -34,12 +42,34 @@ struct CountCons {
         total += acc;
         acc = 0;
     }
-    FS_D bool chunk(const QueryConst& q, int, bool valid, int32_t r, int32_t, int32_t)
+    FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t, int32_t)
     {
-        if (valid) acc += pair_count<TAB>(q, E, r);
+        if (valid) {
+            if (TAB) {
+                const uint32_t qq = div32((uint32_t)r, q.dv_lcm);
+                const uint32_t w = (uint32_t)r - qq * q.lcm;
+                const uint32_t m = Eb[(w & ~31u) | (uint32_t)lane];
+                acc += qq + (__funnelshift_r(m, m, w) & 1u);
+            } else {
+                acc += pair_count<false>(q, (const int8_t*)nullptr, r);
+            }
+        }
         return false;
     }
 };
+
+// The replicated bitmask of E (see CountCons) from the byte table, by a block:
+// word k holds bit i = [E[32 k + i] > 0].
+FS_D void build_count_bitmask(const int8_t* E, uint32_t lcm, uint32_t* Eb)
+{
+    const uint32_t lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const uint32_t words = (lcm + 31) >> 5;
+    for (uint32_t k = threadIdx.x >> 5; k < words; k += nw) {
+        const uint32_t w = k * 32 + lane;
+        const uint32_t m = __ballot_sync(FULL, w < lcm && E[w] > 0);
+        Eb[k * 32 + lane] = m;
+    }
+}
 
 template <bool TAB, bool PER_SLICE>
 __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ QueryConst q,
@@ -50,11 +80,10 @@ __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ Quer
     extern __shared__ __align__(16) unsigned char dyn[];
     load_smemq(q, sq);
     if (threadIdx.x == 0) bsum = 0;
-    int8_t* E = (int8_t*)dyn;
-    if (TAB)
-        for (uint32_t i = threadIdx.x; i < q.lcm; i += blockDim.x) E[i] = sc.E[i];
+    uint32_t* Eb = (uint32_t*)dyn;
+    if (TAB) build_count_bitmask(sc.E, q.lcm, Eb);
     __syncthreads();
-    CountCons<TAB, PER_SLICE> cons{E, sc.slice_cnt, 0, 0, sc.ctr};
+    CountCons<TAB, PER_SLICE> cons{Eb, sc.slice_cnt, 0, 0, sc.ctr};
     run_queue(q, sq, sc, queue, cons);
     uint64_t v = warp_sum_u64(cons.total);
     if ((threadIdx.x & 31) == 0) atomicAdd(&bsum, (unsigned long long)v);
@@ -84,6 +113,8 @@ struct LenCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = 30;
+    static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -168,6 +199,125 @@ __global__ void __launch_bounds__(256) k_pair_len(const __grid_constant__ QueryC
 }
 
 // ===========================================================================
+// length histogram: one difference array per warp, in shared memory
+// ===========================================================================
+// With r = qq lcm + w, the pair's solutions at a leaf have lengths (beyond the
+// leaf's own prefix length lpa = lp + a) from e0 = L0[w] + qq u to
+// e1 = L1[w] + qq v in steps of delta, where L0 = X0 + YD and
+// L1 = L0 + (E - 1) delta (E = [YD >= 0]; c = qq + E solutions).  The
+// difference array takes +1 at the lower end and -1 one step s = |delta| past
+// the upper end: lo = lpa + TL[w].x + qq clo and hp = lpa + TL[w].y + qq chp,
+// (clo, chp) = (v, u) when delta < 0 (e1 is the lower end), (u, v) when
+// delta > 0.  Then hp - lo = c s, so a leaf has solutions iff lo < hp.  Every
+// leaf the walk visits has a residual divisible by G (common-divisor
+// skipping), so w always has solutions in its class; the bound check on hp
+// only keeps a wrong index from reaching memory.
+//
+// Each warp adds into its own 32-bit array (lanes of one warp may still meet
+// on a bin, hence the shared-memory atomics); a bin of it changes by at most
+// one per visited leaf, so a warp flushes its array into the global 64-bit one
+// before 2^31 leaves have been added to it, and the block sums its warps'
+// arrays into the global one at the end.  The count, the minimum and the
+// maximum come from the finished histogram (k_len_finalize).
+struct HistCons {
+    const int2* TL;
+    uint32_t* Dw;  // this warp's difference array (wrapping 32-bit)
+    uint64_t* Dg;  // the global difference array (wrapping 64-bit)
+    int32_t clo, chp;
+    uint32_t dbins;
+    uint32_t since;  // visited leaves added to Dw since it was last flushed (warp-uniform)
+    uint64_t* ctr;
+    static constexpr int UNROLL = 2;
+    static constexpr bool SKIP = true;
+    static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = 14;
+    static constexpr bool R_INDEXED = false;
+    FS_D void fault() { flag_fault(ctr); }
+    FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
+    FS_D void flush()
+    {
+        __syncwarp();
+        for (uint32_t i = threadIdx.x & 31; i < dbins; i += 32) {
+            const uint32_t v = Dw[i];
+            if (v) {
+                atomicAdd((unsigned long long*)&Dg[i], (unsigned long long)(int64_t)(int32_t)v);
+                Dw[i] = 0;
+            }
+        }
+        __syncwarp();
+    }
+    // the walk announces the visited leaves of each sibling group before it
+    // takes them (warp-uniform, fewer than 2^31)
+    FS_D void group_leaves(uint32_t tot)
+    {
+        if (since + tot >= 0x80000000u) {
+            flush();
+            since = 0;
+        }
+        since += tot;
+    }
+    FS_D void slice_begin(const QueryConst&, uint64_t) {}
+    FS_D void slice_end(const QueryConst&, uint64_t) {}
+    FS_D bool chunk(const QueryConst& q, int, bool valid, int32_t r, int32_t a, int32_t lp)
+    {
+        if (valid) {
+            const uint32_t qq = div32((uint32_t)r, q.dv_lcm);
+            const int32_t w = r - (int32_t)(qq * q.lcm);
+            const int2 t = TL[w];
+            const int32_t lpa = lp + a;
+            const int32_t lo = lpa + t.x + (int32_t)qq * clo;
+            const int32_t hp = lpa + t.y + (int32_t)qq * chp;
+            if ((uint32_t)lo < (uint32_t)hp && (uint32_t)hp < dbins) {
+                atomicAdd(&Dw[lo], 1u);
+                atomicAdd(&Dw[hp], 0xffffffffu);  // -1 modulo 2^32
+            }
+        }
+        return false;
+    }
+};
+
+// Per-warp 32-bit arrays (dbins rounded up to 32 words each) and the packed
+// endpoint table (lcm int2) in dynamic shared memory.
+static int hist_smem_bytes(const QueryConst& q, int threads)
+{
+    return (int)q.lcm * 8 + (threads / 32) * ((q.dbins + 31) & ~31) * 4;
+}
+
+__global__ void __launch_bounds__(256) k_pair_hist(const __grid_constant__ QueryConst q,
+                                                   Scratch sc, int queue)
+{
+    __shared__ SmemQ sq;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    load_smemq(q, sq);
+    const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5;
+    int2* TL = (int2*)dyn;
+    uint32_t* D0 = (uint32_t*)(TL + q.lcm);
+    const int dstride = (q.dbins + 31) & ~31;
+    for (int i = threadIdx.x; i < dstride * nwarps; i += blockDim.x) D0[i] = 0;
+    const int32_t s = q.delta < 0 ? -q.delta : q.delta;
+    for (uint32_t w = threadIdx.x; w < q.lcm; w += blockDim.x) {
+        const int32_t x0 = sc.X0[w], yd = sc.YD[w];
+        int2 t = make_int2(1, 0);  // no solutions in this class (never visited)
+        if (x0 >= 0) {
+            const int32_t L0 = x0 + yd, L1 = yd >= 0 ? L0 : L0 - q.delta;
+            t = q.delta < 0 ? make_int2(L1, L0 + s) : make_int2(L0, L1 + s);
+        }
+        TL[w] = t;
+    }
+    __syncthreads();
+    HistCons cons{TL,      D0 + wid * dstride, sc.D, q.delta < 0 ? q.v : q.u, q.delta < 0 ? q.u : q.v,
+                  (uint32_t)q.dbins, 0u, sc.ctr};
+    run_queue(q, sq, sc, queue, cons);
+    __syncthreads();
+    // the block's warp arrays, summed, into the global array
+    for (int i = threadIdx.x; i < q.dbins; i += blockDim.x) {
+        int64_t v = 0;
+        for (int k = 0; k < nwarps; k++) v += (int32_t)D0[k * dstride + i];
+        if (v) atomicAdd((unsigned long long*)&sc.D[i], (unsigned long long)v);
+    }
+}
+
+// ===========================================================================
 // any: does some factorization satisfy the linear predicate?
 // ===========================================================================
 // Along a leaf the predicate's linear form is V0 + t * dw (t = 0..c-1), so each
@@ -209,6 +359,8 @@ struct AnyCons {
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = 30;
+    static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst& q, const RunPrefix& rp, int lane, int32_t ac, int32_t lpc)
     {
@@ -288,6 +440,8 @@ struct TripleCons {
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
     static constexpr bool ANY_ORDER = true;
+    static constexpr uint32_t CHUNK_OPS = MODE ? 12 : 4;
+    static constexpr bool R_INDEXED = true;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -622,14 +776,25 @@ static bool tab_for(const QueryConst& q, Op op)
     return (op == OP_COUNT || op == OP_SLICES) ? q.tab_e != 0 : q.tab_xy != 0;
 }
 
+// The length walk keeps one 32-bit difference array per warp when the pair
+// tables are in use, the lengths step (delta != 0), and the arrays of a block
+// fit in HIST_WARP_SMEM_MAX; otherwise one 64-bit array per block (or the
+// global one) with the in-walk count, min and max (k_pair_len).
+constexpr int HIST_WARP_SMEM_MAX = 64 * 1024;
+static bool hist_per_warp(const QueryConst& q, int threads)
+{
+    return q.tab_xy && q.delta != 0 && hist_smem_bytes(q, threads) <= HIST_WARP_SMEM_MAX;
+}
+
 int pair_smem_bytes(const QueryConst& q, Op op, int threads, int elem_bytes)
 {
     const bool tab = tab_for(q, op);
     switch (op) {
     case OP_COUNT:
     case OP_SLICES:
-        return tab ? (int)q.lcm : 0;
+        return tab ? (int)(((q.lcm + 31) & ~31u) * 4) : 0;
     case OP_LEN: {
+        if (hist_per_warp(q, threads)) return hist_smem_bytes(q, threads);
         int b = tab ? (int)q.lcm * 8 : 0;
         if (q.dbins <= 4096) b += q.dbins * 8;
         return b;
@@ -670,6 +835,7 @@ cudaError_t pair_occupancy(const QueryConst& q, Op op, int threads, int elem_byt
         return tab ? occ(k_pair_count<true, true>, threads, smem, nb)
                    : occ(k_pair_count<false, true>, threads, smem, nb);
     case OP_LEN:
+        if (hist_per_warp(q, threads)) return occ(k_pair_hist, threads, smem, nb);
         if (q.dbins <= 4096)
             return tab ? occ(k_pair_len<true, true>, threads, smem, nb)
                        : occ(k_pair_len<false, true>, threads, smem, nb);
@@ -699,6 +865,7 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
         return tab ? go(k_pair_count<true, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr)
                    : go(k_pair_count<false, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr);
     case OP_LEN:
+        if (hist_per_warp(q, lc.threads)) return go(k_pair_hist, g, b, smem, st, q, sc, queue);
         if (q.dbins <= 4096)
             return tab ? go(k_pair_len<true, true>, g, b, smem, st, q, sc, queue)
                        : go(k_pair_len<false, true>, g, b, smem, st, q, sc, queue);

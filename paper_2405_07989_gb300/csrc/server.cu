@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/fs.h"
+#include "launch.h"
 
 namespace {
 
@@ -321,8 +322,8 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
         s->slots.push_back(sl);
     }
     if (st == FS_OK) {
-        if (cudaMalloc((void**)&s->pool.base, s->cfg.mem_budget_bytes) != cudaSuccess ||
-            cudaMalloc((void**)&s->enum_dcount, 8) != cudaSuccess ||
+        if (fsi::dev_alloc((void**)&s->pool.base, s->cfg.mem_budget_bytes) != cudaSuccess ||
+            fsi::dev_alloc((void**)&s->enum_dcount, 8) != cudaSuccess ||
             cudaStreamCreateWithFlags(&s->enum_st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->enum_ev, cudaEventDisableTiming) != cudaSuccess)
             st = FS_E_NOMEM;

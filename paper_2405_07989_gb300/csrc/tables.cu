@@ -258,14 +258,51 @@ __global__ void __launch_bounds__(1024) k_scan_slices(const uint64_t* cnt, uint6
 // hist[l] = sum_{j >= 0} D[l - j s] for l = 0..maxlen (s = |delta| for the
 // strided difference array of the PAIR walk; s = 0 means D already is the
 // histogram, as the PLAIN walk writes it).  In place on D, then copied to `hist` if given.
+// Finishes the histogram (a strided prefix sum of the difference array when
+// s > 0), copies it to the caller, and takes the count, the minimum and the
+// maximum length from it into the call's counters.
 __global__ void __launch_bounds__(1024) k_len_finalize(const __grid_constant__ QueryConst q,
-                                                       uint64_t* D, uint64_t* hist, int s)
+                                                       uint64_t* D, uint64_t* hist, int s,
+                                                       uint64_t* ctr)
 {
     __shared__ uint64_t part[1024];
+    __shared__ uint64_t wsum[32];
+    __shared__ uint32_t wmin[32], wmax[32];
     const int len = q.maxlen + 1;
     if (s > 0) block_strided_prefix_sum(D, q.dv_in, D, len, s, part);
-    if (hist)
-        for (int l = threadIdx.x; l < len; l += blockDim.x) hist[l] = D[l];
+    uint64_t sum = 0;
+    uint32_t mn = 0xffffffffu, mx = 0;
+    for (int l = threadIdx.x; l < len; l += blockDim.x) {
+        const uint64_t v = D[l];
+        if (hist) hist[l] = v;
+        if (v) {
+            sum += v;
+            mn = min(mn, (uint32_t)l);
+            mx = max(mx, (uint32_t)l);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(FULL, sum, o);
+        mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+        mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        wsum[w] = sum;
+        wmin[w] = mn;
+        wmax[w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; k++) {
+            sum += wsum[k];
+            mn = min(mn, wmin[k]);
+            mx = max(mx, wmax[k]);
+        }
+        ctr[CTR_COUNT] = sum;
+        ctr[CTR_MINC] = sum ? 0xffffffffull - mn : 0ull;
+        ctr[CTR_MAX] = sum ? mx : 0u;
+    }
 }
 
 __global__ void k_copy_u64(const uint64_t* src, uint64_t* dst) { *dst = *src; }
@@ -328,7 +365,7 @@ cudaError_t launch_plan(const QueryConst& q, const Scratch& sc, uint64_t S_req, 
 cudaError_t launch_len_finalize(const QueryConst& q, const Scratch& sc, uint64_t* hist, int s,
                                 cudaStream_t st)
 {
-    k_len_finalize<<<1, 1024, 0, st>>>(q, sc.D, hist, s);
+    k_len_finalize<<<1, 1024, 0, st>>>(q, sc.D, hist, s, sc.ctr);
     return cudaGetLastError();
 }
 

@@ -498,14 +498,54 @@ FS_D void skip_class(const QueryConst& q, uint32_t R, uint32_t b, uint32_t nh, u
     cnt = off < nh ? div32(nh - 1 - off, q.dv_skm[0]) + 1 : 0;
 }
 
+// Issue slots a warp step costs in each way through a sibling group, for the
+// choice in walk_slice_packed: a step over one run's 32 leaves (residual and
+// coordinate advanced once per step), a step with each lane on its own run
+// (plus the lane's own bound check), a packed step (plus the 5-step search for
+// each lane's run).  Cons::CHUNK_OPS estimates the consumer's per-leaf work.
+// Cons::R_INDEXED says it reads a shared 32-bit table at the residual itself:
+// lanes whose residuals are k apart then meet 2^ctz(k)-way bank conflicts
+// (k = hsib for lanes on sibling runs, k = the step between visited leaves
+// for lanes on one run), each extra way costing about a few issue slots.
+template <class Cons>
+struct WalkCost {
+    static constexpr uint32_t full = Cons::CHUNK_OPS + 2;
+    static constexpr uint32_t lane = Cons::CHUNK_OPS + 4;
+    static constexpr uint32_t pack = Cons::CHUNK_OPS + 22;
+    static constexpr uint32_t per_way = 4;
+};
+
+FS_D uint32_t conflict_ways(uint32_t stride)
+{
+    return stride == 0 ? 32u : 1u << min(5, __ffs(stride) - 1);
+}
+
+// Whether a consumer wants each sibling group's visited-leaf total before the
+// group is walked (Cons::group_leaves(uint32_t), warp-uniform, below 2^31).
+template <class C, class = void>
+struct HasGroupLeaves {
+    static constexpr bool value = false;
+};
+template <class C>
+struct HasGroupLeaves<C, decltype((void)&C::group_leaves)> {
+    static constexpr bool value = true;
+};
+
 // The walk for consumers that do not depend on the order of the leaves inside
-// a slice (Cons::ANY_ORDER: counts, length statistics, predicates).  Each run's
-// full 32-leaf steps are taken run by run (lane l takes the run's leaves l,
-// l + 32, ..), then the remainders of all runs of the group (fewer than 32
-// leaves each) are packed into shared steps: lane l of such a step finds its
-// run by a 5-step search over the runs' offsets.  Short runs no longer cost a
-// step each, and the per-run bookkeeping is done once per group by all lanes
-// together.
+// a slice (Cons::ANY_ORDER: counts, length statistics, predicates).  A group of
+// up to 32 sibling runs is taken in one of two ways, chosen per group from the
+// runs' visited-leaf counts cnt_j (q.walk can force either):
+//  - lanes: lane j walks run j by itself, all lanes stepping together until the
+//    longest run is done (max cnt_j steps; a lane whose run is done idles);
+//  - packed: each run's full 32-leaf steps run by run (lane l takes the run's
+//    leaves l, l + 32, ..), then the remainders of all runs (fewer than 32
+//    leaves each) packed into shared steps, lane l of such a step finding its
+//    run by a 5-step search over the runs' offsets (sum_j floor(cnt_j / 32)
+//    full steps and ceil(sum_j (cnt_j mod 32) / 32) packed ones).
+// Sibling runs differ in length by about hsib / h_in leaves per lane, so when
+// runs are a few dozen leaves long the lanes way wastes little and avoids the
+// packed steps' search; with long runs or few siblings the packed way wins.
+// The per-run bookkeeping is done once per group by all lanes together.
 template <class Cons>
 FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32* dvh,
                             const int32_t* starts, uint64_t s, uint64_t nleaves, int lane,
@@ -552,55 +592,92 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
         if (skip && nh > 0) skip_class(q, Rj, bj, nh, first, cnt, mj);
         const uint32_t nfull = cnt >> 5, part = cnt & 31;
         cons.group_begin(q, rp, lane, ac, lpc);
-        // the full steps, run by run: lane l takes the run's leaves l, l + 32, ..
-        for (uint32_t m = __ballot_sync(FULL, nfull > 0); m; m &= m - 1) {
-            const int j = __ffs(m) - 1;
-            const uint32_t nf = __shfl_sync(FULL, nfull, j);
-            uint32_t a = __shfl_sync(FULL, first, j) + (uint32_t)lane * ma;
-            uint32_t r = __shfl_sync(FULL, Rj, j) - a * hin;
-            const int32_t lp = lpc + j;
+        if constexpr (HasGroupLeaves<Cons>::value) cons.group_leaves(__reduce_add_sync(FULL, cnt));
+        const uint32_t mxc = __reduce_max_sync(FULL, cnt);
+        bool lanes = q.walk == FS_WALK_LANES;
+        if (q.walk == FS_WALK_AUTO) {
+            const uint32_t sfull = __reduce_add_sync(FULL, nfull);
+            const uint32_t spart = __reduce_add_sync(FULL, part);
+            using C = WalkCost<Cons>;
+            uint32_t cl = C::lane, cf = C::full, cp = C::pack;
+            if (Cons::R_INDEXED) {
+                cl += (conflict_ways(hsib) - 1) * C::per_way;
+                cf += (conflict_ways(mstep) - 1) * C::per_way;
+                cp += C::per_way;  // lanes on mixed runs: about two ways
+            }
+            lanes = (uint64_t)mxc * cl <= (uint64_t)sfull * cf + (uint64_t)((spart + 31) >> 5) * cp;
+        }
+        if (lanes) {
+            // lane j: run j's visited leaves a = first + i ma, i < cnt
+            uint32_t a = first, r = Rj - first * hin;
+            const int32_t lp = lpc + lane;
             uint32_t i = 0;
             if (Cons::UNROLL > 1) {
-                for (; i + Cons::UNROLL <= nf; i += Cons::UNROLL) {
+                for (; i + Cons::UNROLL <= mxc; i += Cons::UNROLL) {
 #pragma unroll
                     for (int u = 0; u < Cons::UNROLL; u++) {
-                        if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                        r -= 32u * mstep;
-                        a += 32u * ma;
+                        if (cons.chunk(q, lane, i + u < cnt, (int32_t)r, (int32_t)a, lp)) return true;
+                        r -= mstep;
+                        a += ma;
                     }
                 }
             }
-            for (; i < nf; i++) {
-                if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
-                r -= 32u * mstep;
-                a += 32u * ma;
+            for (; i < mxc; i++) {
+                if (cons.chunk(q, lane, i < cnt, (int32_t)r, (int32_t)a, lp)) return true;
+                r -= mstep;
+                a += ma;
             }
-        }
-        // the remainders, packed: run j's last `part` visited leaves
-        const uint32_t pa = first + (cnt - part) * ma;  // the first of them
-        const uint32_t r0 = Rj - pa * hin;
-        uint32_t iv = part;  // remainder leaves of runs 0..j
+        } else {
+            // the full steps, run by run: lane l takes the run's leaves l, l + 32, ..
+            for (uint32_t m = __ballot_sync(FULL, nfull > 0); m; m &= m - 1) {
+                const int j = __ffs(m) - 1;
+                const uint32_t nf = __shfl_sync(FULL, nfull, j);
+                uint32_t a = __shfl_sync(FULL, first, j) + (uint32_t)lane * ma;
+                uint32_t r = __shfl_sync(FULL, Rj, j) - a * hin;
+                const int32_t lp = lpc + j;
+                uint32_t i = 0;
+                if (Cons::UNROLL > 1) {
+                    for (; i + Cons::UNROLL <= nf; i += Cons::UNROLL) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, iv, o);
-            if (lane >= o) iv += t;
-        }
-        const uint32_t ev = iv - part;
-        const uint32_t tot = __shfl_sync(FULL, iv, 31);
-        for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
-            const uint32_t t = t0 + (uint32_t)lane;
-            // the run of visited leaf t: the last j with ev_j <= t (runs past
-            // the group's end have ev_j = tot)
-            int j = 0;
-#pragma unroll
-            for (int st = 16; st >= 1; st >>= 1) {
-                const uint32_t e = __shfl_sync(FULL, ev, j + st);
-                if (e <= t) j += st;
+                        for (int u = 0; u < Cons::UNROLL; u++) {
+                            if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                            r -= 32u * mstep;
+                            a += 32u * ma;
+                        }
+                    }
+                }
+                for (; i < nf; i++) {
+                    if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                    r -= 32u * mstep;
+                    a += 32u * ma;
+                }
             }
-            const uint32_t k = t - __shfl_sync(FULL, ev, j);
-            const uint32_t a = __shfl_sync(FULL, pa, j) + k * ma;
-            const uint32_t r = __shfl_sync(FULL, r0, j) - k * mstep;
-            if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lpc + j)) return true;
+            // the remainders, packed: run j's last `part` visited leaves
+            const uint32_t pa = first + (cnt - part) * ma;  // the first of them
+            const uint32_t r0 = Rj - pa * hin;
+            uint32_t iv = part;  // remainder leaves of runs 0..j
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, iv, o);
+                if (lane >= o) iv += t;
+            }
+            const uint32_t ev = iv - part;
+            const uint32_t tot = __shfl_sync(FULL, iv, 31);
+            for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+                const uint32_t t = t0 + (uint32_t)lane;
+                // the run of visited leaf t: the last j with ev_j <= t (runs past
+                // the group's end have ev_j = tot)
+                int j = 0;
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const uint32_t e = __shfl_sync(FULL, ev, j + st);
+                    if (e <= t) j += st;
+                }
+                const uint32_t k = t - __shfl_sync(FULL, ev, j);
+                const uint32_t a = __shfl_sync(FULL, pa, j) + k * ma;
+                const uint32_t r = __shfl_sync(FULL, r0, j) - k * mstep;
+                if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lpc + j)) return true;
+            }
         }
         const uint64_t took = __shfl_sync(FULL, ir, (int)ns - 1);
         if (took >= rem) return false;
