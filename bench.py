@@ -59,7 +59,7 @@ def measured_peaks():
 
 
 # the translation unit that defines each profiled kernel
-KERNEL_SOURCE = {"pair_enum": "enum_fixed.cu"}
+KERNEL_SOURCE = {"pair_enum": "enum_fixed.cu", "pair_count": "pair.cu", "quad_count": "pair.cu"}
 
 
 def strip_c_comments(src: str) -> str:
@@ -123,6 +123,42 @@ def recorded_traffic(kernel: str):
     if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def recorded_instructions(kernel: str):
+    """Warp instructions per pipe of one launch of `kernel` on the heavy count
+    query, from a committed ncu summary, if it was taken on the current kernel
+    sources; else None."""
+    p = os.path.join(ROOT, "profiles", "count_inst.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    e = rec.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
+        return None
+    return e
+
+
+def numa_placement(index: int) -> dict:
+    """The host's NUMA nodes and the GPU's node (from sysfs), for the pinned
+    buffer's placement; empty where sysfs does not say."""
+    out = {}
+    base = "/sys/devices/system/node"
+    if os.path.isdir(base):
+        out["host_nodes"] = sorted(x for x in os.listdir(base) if x.startswith("node") and x[4:].isdigit())
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().lower()
+        for cand in (bus, bus[-12:]):
+            p = f"/sys/bus/pci/devices/{cand}/numa_node"
+            if cand and os.path.exists(p):
+                out["gpu_node"] = int(open(p).read().strip())
+                break
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    return out
 
 
 class ClockSampler:
@@ -434,21 +470,42 @@ def run_gpu(args):
         assert c1 == Z and c2 == Z
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws, dev)
     assert torch.equal(host.view(-1, d)[:4].to(dev), out.view(-1, d)[:4])
+    # the link's own ceiling: one plain device-to-host copy of the same bytes
+    # into the same pinned buffer, event-timed
+    host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record()
+    for _ in range(3):
+        host.copy_(out, non_blocking=True)
+    l1.record()
+    torch.cuda.synchronize()
+    link_gbs = Z * row_bytes / (l0.elapsed_time(l1) / 3 / 1000.0) / 1e9
     e2e = {"value": replica_value(Z, ws, e2e_s * 1000.0), "unit": "factorizations/s",
            "h2d_bytes_per_step": 2 * d * 4,
            # rows, three counter reads (128 B each) and the slice offsets
            "d2h_bytes_per_step": Z * row_bytes + 3 * 128 + 8 * (S_enum + 1),
            "ms_per_step": e2e_s * 1000.0,
-           "path": "fs_count + fs_enumerate_host into pinned host memory"}
+           "path": "fs_count + fs_enumerate_host into pinned host memory",
+           "d2h_link_ceiling_gbs": link_gbs,
+           "link_frac": (Z * row_bytes / e2e_s / 1e9) / link_gbs,
+           "link_note": "plain cudaMemcpyAsync of the same bytes into the same pinned buffer",
+           "numa": numa_placement(local)}
 
     # ---- extras: the integer-bound count walk on the heavy count-only query ----
     extras = None
     if not args.no_extras:
         extras = heavy_count_extras(fs, workloads, dev)
+        # the integer-bound count kernel's roofline beside the dominant kernel's
+        roofline["count"] = extras["count_roofline"]
+        roofline["count_quad"] = extras["count_quad_roofline"]
         extras["batched"] = batch_extras(fs, workloads, dev)
         extras["serving"] = serving_extras(fs, workloads, args.serve_rate, args.serve_requests)
         # capacity: the same requests all at once (no arrival pacing)
         extras["serving_saturated"] = serving_extras(fs, workloads, 1e9, args.serve_requests)
+        # the same without the histograms (count and length range only)
+        extras["serving_saturated_no_hist"] = serving_extras(fs, workloads, 1e9, args.serve_requests,
+                                                             hist=False)
         extras["table1_context"] = table1_extras(fs, dev)
         extras["methods"] = method_extras(fs, workloads, dev)
 
@@ -487,21 +544,65 @@ def run_gpu(args):
     return 0
 
 
-# Integer operations the PAIR count walk spends on one leaf in closed form: residual
-# step, quotient (multiply-high + shift), remainder (multiply-subtract), table
-# load, add, clamp, accumulate.
+# Integer operations of the PAIR count's closed form at one visited leaf:
+# quotient by the lcm (multiply-high, shift), remainder (multiply-subtract),
+# the class bit's index, its load, its extraction (shift, mask), and the add.
 COUNT_OPS_PER_LEAF = 8
 
 
-def visited_leaves(leaves: int, gens) -> int:
-    """The leaves the PAIR walk (descending order) resolves: those whose
-    residual is a multiple of G = gcd of the last two generators, since only
-    they can complete (Sec. 3.2.4).  With the innermost walk generator h, a
-    run's residuals step by h, so a fraction gcd(h, G) / G of a run's leaves
-    qualifies and a fraction 1 / gcd(h, G) of the runs has any: leaves / G
-    in all, up to a leaf per run."""
+def visited_leaves(fs, n, gens) -> int:
+    """The leaves the PAIR count walk resolves, exactly: a leaf (a prefix of
+    the first d-2 generators in descending order, residual r = n - phi) is
+    visited iff G = gcd of the last two generators divides r (common-divisor
+    skipping), i.e. iff phi + t G = n for some t >= 0.  So their number is the
+    factorization count of n over the first d-2 generators and G."""
     w = sorted(gens, reverse=True)
-    return leaves // math.gcd(w[-1], w[-2]) if len(w) >= 3 else leaves
+    if len(w) < 3:
+        return 0
+    return fs.fs_count(n, w[:-2] + [math.gcd(w[-1], w[-2])])
+
+
+# Integer operations of the trailing-four count at one leaf: the table entry's
+# address, its load, and the add.
+QUAD_OPS_PER_LEAF = 3
+
+
+def quad_leaves(fs, n, gens) -> int:
+    """The leaves of the trailing-four (QUAD) count walk, exactly: prefixes of
+    the first d-4 generators (descending) with phi <= n, i.e. the
+    factorizations of n over those generators and a slack generator 1."""
+    w = sorted(gens, reverse=True)
+    return fs.fs_count(n, w[:-4] + [1]) if len(w) >= 5 else 0
+
+
+def count_roofline(fs, n, g, walk_ms, rates, key="pair_count"):
+    """A count walk against the probed 32-bit add rate (128 lanes per clock
+    per SM: the ALU and FMA pipes together).  `frac` is its integer-pipe
+    issue: the ALU- and FMA-pipe warp instructions of one launch, counted by
+    ncu on the same kernel sources at this size (profiles/count_inst.json),
+    x 32 lanes / the walk's event-timed duration here.  `useful_frac` counts
+    only the closed form's operations per leaf it resolves (PAIR: the visited
+    leaves, COUNT_OPS_PER_LEAF each; QUAD: every leaf, QUAD_OPS_PER_LEAF)."""
+    if key == "pair_count":
+        units, ops, kernel = visited_leaves(fs, n, g), COUNT_OPS_PER_LEAF, "k_pair_count"
+    else:
+        units, ops, kernel = quad_leaves(fs, n, g), QUAD_OPS_PER_LEAF, "k_triple_walk (QUAD)"
+    peak = rates["add"]
+    useful = units * ops / (walk_ms / 1000.0)
+    rec = recorded_instructions(key)
+    out = {"bound": "alu", "kernel": kernel, "workload": f"g={tuple(g)}, n={n}",
+           "unit": "int32 lane-ops/s", "peak": peak, "peak_source": "probed add rate (fs_probe_int_rate)",
+           "avg_launch_ms": walk_ms, "leaves_resolved": units,
+           "useful_ops_per_leaf": ops, "useful_frac": useful / peak,
+           "achieved": None, "frac": None}
+    if rec and rec.get("n") == n and list(rec.get("gens", [])) == list(g):
+        ints = rec["alu_warp_inst"] + rec["fma_warp_inst"]
+        ach = ints * 32 / (walk_ms / 1000.0)
+        out.update({"achieved": ach, "frac": ach / peak, "int_warp_inst_per_launch": ints,
+                    "warp_inst_per_launch": rec["warp_inst"],
+                    "warp_inst_per_leaf": rec["warp_inst"] / units if units else None,
+                    "inst_source": "ncu counters of the same kernel sources, profiles/count_inst.json"})
+    return out
 
 
 def heavy_count_extras(fs, workloads, dev):
@@ -536,9 +637,11 @@ def heavy_count_extras(fs, workloads, dev):
     Z3, ms3, walk3, prof3 = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count")
     Z4, ms4, walk4, prof4 = timed_count(None, "quad_count")
     assert Z3 == Z and Z4 == Z
-    visited = visited_leaves(leaves, g)
-    achieved = visited * COUNT_OPS_PER_LEAF / (walk_ms / 1000.0)
+    roof = count_roofline(fs, n, g, walk_ms, rates)
+    roof_quad = count_roofline(fs, n, g, walk4, rates, key="quad_count")
     hist = torch.zeros(n // min(g) + 1, dtype=torch.int64, device=dev)
+    fs.fs_length_stats(n, g, hist)  # warm-up
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     cnt, mn, mx = fs.fs_length_stats(n, g, hist)
     len_s = time.perf_counter() - t0
@@ -555,15 +658,15 @@ def heavy_count_extras(fs, workloads, dev):
         z3, ms3s, _, _ = timed_count(fs.make_config(method=fs.METHOD_TRIPLE), "triple_count", ns, gs)
         z4, ms4s, _, _ = timed_count(None, "quad_count", ns, gs)
         assert z3 == zs and z4 == zs
-        vs = visited_leaves(lv, gs)
+        vs = visited_leaves(fs, ns, gs)
         seeds[str(seed)] = {"gens": list(gs), "n": ns, "factorizations": zs, "leaves": lv,
                             "leaves_visited": vs,
                             "count_ms": mss, "count_leaves_per_s": lv / (wms / 1000.0),
-                            "count_roofline_frac": vs * COUNT_OPS_PER_LEAF / (wms / 1000.0) / rates["add"],
+                            "count_useful_frac": vs * COUNT_OPS_PER_LEAF / (wms / 1000.0) / rates["add"],
                             "count_triple_ms": ms3s, "count_quad_ms": ms4s}
     return {
         "workload": f"count-only heavy query g={tuple(g)}, n={n}",
-        "factorizations": Z, "leaves": leaves, "leaves_visited": visited,
+        "factorizations": Z, "leaves": leaves, "leaves_visited": roof["leaves_resolved"],
         "count_ms": ms, "count_walk_ms": walk_ms,
         "count_factorizations_per_s": Z / (ms / 1000.0), "count_leaves_per_s": leaves / (walk_ms / 1000.0),
         "count_triple_ms": ms3, "count_triple_walk_ms": walk3,
@@ -572,13 +675,12 @@ def heavy_count_extras(fs, workloads, dev):
         "count_quad_ms": ms4, "count_quad_walk_ms": walk4,
         "count_quad_factorizations_per_s": Z / (ms4 / 1000.0),
         "count_quad_breakdown_ms": {k: v[1] for k, v in prof4.items()},
-        "count_roofline": {"bound": "alu", "achieved": achieved, "peak": rates["add"],
-                           "unit": "int32 lane-ops/s", "frac": achieved / rates["add"],
-                           "ops_per_leaf": COUNT_OPS_PER_LEAF, "per": "visited leaf",
-                           "peak_source": "probed add rate"},
+        "count_roofline": roof,
+        "count_quad_roofline": roof_quad,
         "int_rates": rates,
         "length_stats_s": len_s, "length_min_max": [mn, mx],
         "length_factorizations_per_s": Z / len_s,
+        "length_stats_vs_count": len_s / (walk_ms / 1000.0),
         "length_min_max_only_s": len_minmax_s,
         "other_seeds": seeds,
     }
@@ -707,23 +809,31 @@ def batch_extras(fs, workloads, dev):
     return out
 
 
-def serving_extras(fs, workloads, rate: float, nreq: int):
+def serving_extras(fs, workloads, rate: float, nreq: int, hist: bool = True):
     """The serving workload: Poisson arrivals of queries drawn like the batched
-    ones with n up to 20000, 80 % count / 15 % length statistics / 5 %
-    enumerate (int16 rows), through the continuous-batching request loop; a
-    client thread releases enumerate rows as soon as they are polled."""
+    ones with n up to 20000, 80 % count / 15 % length statistics (with the
+    length histogram) / 5 % enumerate (int16 rows), through the
+    continuous-batching request loop; a client thread releases rows and
+    histograms as soon as they are polled.  Per stage: queue (submit to batch
+    launch), batch (launch to results), job wait and job (enumerate rows or
+    histogram), answer (results to completion for requests without a job)."""
     import threading
     reqs = workloads.config5(0, nreq, rate, 20000)
     budget = 32 << 30
-    srv = fs.Server(mem_budget_bytes=budget, table_bytes=1 << 30, max_batch=512, slots=3,
-                    window_us=200)
+    scfg = dict(mem_budget_bytes=budget, table_bytes=1 << 30, max_batch=512, slots=3,
+                window_us=200, job_streams=4)
+    srv = fs.Server(**scfg)
+
+    def job_of(r):
+        return r["status"] == fs.FS_OK and r["rows"] != 0
+
     try:
-        warm = [srv.submit(op, n, g) for (_, op, n, g) in reqs[:16]]
+        warm = [srv.submit(op, n, g, hist=hist and op == fs.REQ_LENGTHS) for (_, op, n, g) in reqs[:16]]
         seen = 0
         while seen < len(warm):
             for r in srv.poll(64, wait_ms=50):
                 seen += 1
-                if r["op"] == fs.REQ_ENUMERATE and r["status"] == fs.FS_OK:
+                if job_of(r):
                     srv.release(r["ticket"])
         done = {}
 
@@ -731,7 +841,7 @@ def serving_extras(fs, workloads, rate: float, nreq: int):
             while len(done) < nreq:
                 for r in srv.poll(1024, wait_ms=20):
                     done[r["ticket"]] = r
-                    if r["op"] == fs.REQ_ENUMERATE and r["status"] == fs.FS_OK:
+                    if job_of(r):
                         srv.release(r["ticket"])
 
         th = threading.Thread(target=poller)
@@ -741,30 +851,42 @@ def serving_extras(fs, workloads, rate: float, nreq: int):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            srv.submit(op, n, g, elem_bytes=2)
+            srv.submit(op, n, g, elem_bytes=2, hist=hist and op == fs.REQ_LENGTHS)
         th.join()
     finally:
         srv.close()
     rs = list(done.values())
     lat = np.array([r["t_done"] - r["t_submit"] for r in rs]) * 1000.0
     span = max(r["t_done"] for r in rs) - min(r["t_submit"] for r in rs)
+
+    def pct(v):
+        v = np.asarray(v) * 1000.0
+        return {"n": int(v.size), "p50_ms": float(np.percentile(v, 50)),
+                "p99_ms": float(np.percentile(v, 99))} if v.size else {"n": 0}
+
     by_op = {}
     for op, name in ((fs.REQ_COUNT, "count"), (fs.REQ_LENGTHS, "lengths"),
                      (fs.REQ_ENUMERATE, "enumerate")):
-        l = np.array([(r["t_done"] - r["t_submit"]) * 1000.0 for r in rs if r["op"] == op])
-        if l.size:
-            by_op[name] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)),
-                           "p99_ms": float(np.percentile(l, 99))}
+        by_op[name] = pct([r["t_done"] - r["t_submit"] for r in rs if r["op"] == op])
+    ran = [r for r in rs if r["t_start"] > 0]
+    jobs = [r for r in ran if r["t_job"] > 0]
+    stages = {"queue": pct([r["t_start"] - r["t_submit"] for r in ran]),
+              "batch": pct([r["t_counted"] - r["t_start"] for r in ran]),
+              "job_wait": pct([r["t_job"] - r["t_counted"] for r in jobs]),
+              "job": pct([r["t_done"] - r["t_job"] for r in jobs]),
+              "answer": pct([r["t_done"] - r["t_counted"] for r in ran if r["t_job"] == 0])}
     status = {}
     for r in rs:
         status[fs.status_name(r["status"])] = status.get(fs.status_name(r["status"]), 0) + 1
     return {
         "workload": (f"{nreq} requests, Poisson arrivals at {rate:g}/s, d in [3,8], gens in "
-                     f"[5,100], n in [100,20000], 80/15/5 % count/lengths/enumerate (int16), seed 0"),
-        "server": {"mem_budget_bytes": budget, "max_batch": 512, "slots": 3, "window_us": 200},
+                     f"[5,100], n in [100,20000], 80/15/5 % count/lengths{'+histogram' if hist else ''}"
+                     f"/enumerate (int16), seed 0"),
+        "server": scfg,
         "queries_per_s": nreq / span, "span_s": span,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "by_op": by_op, "status": status,
+        "by_op": by_op, "stages": stages, "status": status,
+        "histograms": sum(1 for r in rs if r["op"] == fs.REQ_LENGTHS and job_of(r)),
         "factorizations_served": int(sum(r["count"] for r in rs if r["status"] == fs.FS_OK)),
     }
 

@@ -195,6 +195,13 @@ fs_status fs_enumerate_ex(int64_t n, const uint32_t* gens, int d, const fs_confi
 fs_status fs_count_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
                          uint64_t* dev_count, void* stream);
 
+/* Enqueues the length statistics (as fs_length_stats_ex): hist_dev (DEVICE,
+ * nullable) receives the histogram, out_dev (DEVICE, nullable) three uint64:
+ * the count, the minimum and the maximum of sum a_i (both 0 when the count is
+ * 0), in stream order.  Argument errors are reported synchronously. */
+fs_status fs_length_stats_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                                uint64_t* hist_dev, uint64_t* out_dev, void* stream);
+
 /* Enqueues the enumeration into dev_buf (as fs_enumerate); *dev_count (DEVICE
  * uint64) receives |Z|.  Rows past cap are dropped; the caller compares
  * *dev_count with cap. */
@@ -317,6 +324,10 @@ fs_status fs_batch_create(const fs_query* queries, int nq, int mode, const fs_co
  *   on `stream` from the batch's pinned buffer; FS_E_CAPACITY if they exceed
  *   the reservation.  Do not load again before that copy has run (order it on
  *   the same stream, or wait).
+ * fs_batch_load_mode: the same, switching the batch to `mode` first (a batch
+ *   reserved for FS_BATCH_LENGTHS can load count-only queries, which need no
+ *   length tables and walk faster, and back); its launch shape is re-derived
+ *   from the new mode's occupancy.
  * fs_batch_fetch: enqueues the copy of the results into pinned host memory.
  * fs_batch_collect: reads the fetched results; the caller waits for the
  *   stream (or an event recorded after fs_batch_fetch) first. */
@@ -325,6 +336,7 @@ fs_status fs_batch_table_bytes(const fs_query* queries, int nq, int mode, const 
 fs_status fs_batch_reserve(int max_queries, uint64_t table_bytes, int mode, const fs_config* cfg,
                            fs_batch** out);
 fs_status fs_batch_load(fs_batch* b, const fs_query* queries, int nq, void* stream);
+fs_status fs_batch_load_mode(fs_batch* b, const fs_query* queries, int nq, int mode, void* stream);
 fs_status fs_batch_fetch(fs_batch* b, void* stream);
 fs_status fs_batch_collect(fs_batch* b, fs_result* results);
 /* Enqueues one complete evaluation of the batch on `stream` (tables, plan,
@@ -359,26 +371,33 @@ fs_status fs_reserve(uint64_t bytes, void* stream);
  * each on its own stream: a free slot takes up to max_batch queued requests
  * (when other batches are running it first lets the batch fill for up to
  * window_us), so requests that arrive while earlier ones are on the GPU are
- * batched and run concurrently with them.  An ENUMERATE request is counted in
- * a batch first; its rows (count * d * elem_bytes bytes, exact) are then
- * admitted against the device memory budget: larger than the whole budget ->
- * FS_E_CAPACITY (count still reported); otherwise it waits until that many
- * bytes are free, is materialised (fs_enumerate_async, one at a time, on the
- * server's enumerate stream) and its rows stay reserved until
- * fs_server_release.  Results are exactly those of the single-query calls.
- * A single query whose tables exceed table_bytes is answered FS_E_CAPACITY.
- * Thread safety: submit / poll / release may be called from any thread.
- * The server's batches own their memory and its enumerates run on a stream
- * of its own, so other library calls may run beside it. */
+ * batched and run concurrently with them.  The batch gives every request its
+ * count and length range.  Two kinds of request then need device work of
+ * their own (a "job"): an ENUMERATE (its rows, count * d * elem_bytes bytes)
+ * and a LENGTHS request with hist = 1 (its histogram, (floor(n / min g) + 1)
+ * * 8 bytes).  A job's bytes, exact, are admitted against the device memory
+ * budget: larger than the whole budget -> FS_E_CAPACITY (count and range still
+ * reported; so is a histogram whose PAIR walk would visit more than
+ * hist_max_leaves leaves, |Z(n; g_1..g_{d-2}, gcd(g_{d-1}, g_d))| in descending
+ * order); otherwise the job waits, in arrival order, until that many bytes
+ * are free and one of `job_streams` job streams is idle, then runs there
+ * (fs_enumerate_async or fs_length_stats_async), several jobs at once; its
+ * output stays reserved until fs_server_release.  Results are exactly those of
+ * the single-query calls.  A single query whose tables exceed table_bytes is
+ * answered FS_E_CAPACITY.  Thread safety: submit / poll / release may be
+ * called from any thread.  The server's batches own their memory and its jobs
+ * run on streams of its own, so other library calls may run beside it. */
 enum { FS_REQ_COUNT = 0, FS_REQ_LENGTHS = 1, FS_REQ_ENUMERATE = 2 };
 
 typedef struct fs_server_config {
-    uint64_t mem_budget_bytes;  /* device bytes for enumerate rows; 0 = 1 GiB */
+    uint64_t mem_budget_bytes;  /* device bytes for job outputs (rows, histograms); 0 = 1 GiB */
     uint64_t table_bytes;       /* table bytes per batch slot; 0 = 256 MiB */
     int32_t max_batch;          /* queries per batch; 0 = 512 */
     int32_t slots;              /* batches in flight; 0 = 3 */
     int32_t window_us;          /* fill window while the GPU is busy; 0 = 200 */
-    int32_t pad;
+    int32_t job_streams;        /* jobs in flight (enumerates, histograms); 0 = 4 */
+    uint64_t hist_max_leaves;   /* a histogram job whose walk visits more leaves is refused
+                                   with FS_E_CAPACITY; 0 = 2^34 */
 } fs_server_config;
 
 typedef struct fs_request {
@@ -388,21 +407,24 @@ typedef struct fs_request {
     int32_t op;               /* FS_REQ_* */
     int32_t elem_bytes;       /* ENUMERATE: 2 (int16) or 4 (int32) */
     int32_t keep_order;       /* ENUMERATE: row order as fs_config.keep_order */
-    int32_t pad;
+    int32_t hist;             /* LENGTHS: 1 = also the length histogram */
 } fs_request;
 
 typedef struct fs_response {
     uint64_t ticket;
     int32_t status;     /* FS_OK or the fs_status that rejected the request */
     int32_t op;
-    uint64_t count;     /* |Z(n, g)| (also for a rejected ENUMERATE when it was counted) */
+    uint64_t count;     /* |Z(n, g)| (also for a rejected job when it was counted) */
     uint32_t min_len;   /* LENGTHS and ENUMERATE: min / max of sum a_i when count > 0 */
     uint32_t max_len;
-    void* rows;         /* ENUMERATE, FS_OK: DEVICE rows [count][d], as fs_enumerate_ex
-                           with the request's keep_order; owned by the server until
-                           fs_server_release(ticket) */
+    void* rows;         /* FS_OK jobs, DEVICE memory owned by the server until
+                           fs_server_release(ticket): ENUMERATE rows [count][d] (as
+                           fs_enumerate_ex with the request's keep_order); LENGTHS with
+                           hist: floor(n / min g) + 1 uint64 bins (as fs_length_stats) */
     double t_submit;    /* seconds since fs_server_create */
-    double t_start;     /* when its batch (or its enumerate) was launched */
+    double t_start;     /* when its batch was launched (the end of its queue wait) */
+    double t_counted;   /* when its batch's results were collected */
+    double t_job;       /* when its job was launched (0: no job) */
     double t_done;      /* when its result was seen complete */
 } fs_response;
 

@@ -65,13 +65,14 @@ REQ_COUNT, REQ_LENGTHS, REQ_ENUMERATE = 0, 1, 2
 class fs_server_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
                 ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
-                ("window_us", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("window_us", ctypes.c_int32), ("job_streams", ctypes.c_int32),
+                ("hist_max_leaves", ctypes.c_uint64)]
 
 
 class fs_request(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("gens", ctypes.c_uint32 * MAX_D),
                 ("op", ctypes.c_int32), ("elem_bytes", ctypes.c_int32),
-                ("keep_order", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("keep_order", ctypes.c_int32), ("hist", ctypes.c_int32)]
 
 
 class fs_response(ctypes.Structure):
@@ -79,6 +80,7 @@ class fs_response(ctypes.Structure):
                 ("count", ctypes.c_uint64), ("min_len", ctypes.c_uint32),
                 ("max_len", ctypes.c_uint32), ("rows", ctypes.c_void_p),
                 ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_counted", ctypes.c_double), ("t_job", ctypes.c_double),
                 ("t_done", ctypes.c_double)]
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -101,6 +103,8 @@ SIGNATURES = {
     "fs_enumerate": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _vp, ctypes.c_uint64,
                                     ctypes.c_int, _u64p, _vp]),
     "fs_count_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _u64p, _vp]),
+    "fs_length_stats_async": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp, _vp, _vp,
+                                             _vp]),
     "fs_length_stats_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
                                           ctypes.POINTER(fs_len_summary), _vp, _vp]),
     "fs_any_ex": (ctypes.c_int, [ctypes.c_int64, _u32p, ctypes.c_int, _cfgp,
@@ -129,6 +133,8 @@ SIGNATURES = {
     "fs_batch_create": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int, _cfgp,
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "fs_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "fs_batch_load_mode": (ctypes.c_int, [_vp, ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int,
+                                          _vp]),
     "fs_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(fs_result), _vp]),
     "fs_batch_destroy": (ctypes.c_int, [_vp]),
     "fs_batch_run": (ctypes.c_int, [ctypes.POINTER(fs_query), ctypes.c_int, ctypes.c_int, _cfgp,
@@ -249,6 +255,16 @@ def fs_length_stats(n: int, gens, hist=None, cfg: fs_config | None = None, strea
     _check(lib().fs_length_stats_ex(int(n), g, d, _cfgp_of(cfg), ctypes.byref(out), _ptr(hist),
                                     _stream(stream)))
     return int(out.count), int(out.min_len), int(out.max_len)
+
+
+def fs_length_stats_async(n: int, gens, hist=None, out=None, cfg: fs_config | None = None,
+                          stream=None) -> None:
+    """Enqueue the length statistics: hist (optional CUDA int64 tensor of
+    floor(n / min g) + 1 bins) receives the histogram, out (optional CUDA int64
+    tensor of 3) the count, min and max, in stream order."""
+    g, d = _gens(gens)
+    _check(lib().fs_length_stats_async(int(n), g, d, _cfgp_of(cfg), _ptr(hist), _ptr(out),
+                                       _stream(stream)))
 
 
 def fs_any(n: int, gens, w, c: int, op: int = 0, modulus: int = 0,
@@ -481,21 +497,67 @@ def fs_reserve(nbytes: int, stream=None) -> None:
     _check(lib().fs_reserve(int(nbytes), _stream(stream)))
 
 
+class BatchSlot:
+    """A reusable batch for request loops (fs_batch_reserve): load() queries of
+    either mode, launch(), then results() after fetch and a wait."""
+
+    def __init__(self, max_queries: int, table_bytes: int, mode: int = BATCH_LENGTHS,
+                 cfg: fs_config | None = None):
+        h = ctypes.c_void_p(0)
+        _check(lib().fs_batch_reserve(int(max_queries), int(table_bytes), int(mode), _cfgp_of(cfg),
+                                      ctypes.byref(h)))
+        self._h = h
+        self.n = 0
+
+    def load(self, queries, mode: int | None = None, stream=None):
+        q = _queries(queries)
+        if mode is None:
+            _check(lib().fs_batch_load(self._h, q, len(queries), _stream(stream)))
+        else:
+            _check(lib().fs_batch_load_mode(self._h, q, len(queries), int(mode), _stream(stream)))
+        self.n = len(queries)
+
+    def launch(self, stream=None):
+        _check(lib().fs_batch_launch(self._h, _stream(stream)))
+        _check(lib().fs_batch_fetch(self._h, _stream(stream)))
+
+    def results(self):
+        import torch
+        torch.cuda.synchronize()
+        res = (fs_result * self.n)()
+        _check(lib().fs_batch_collect(self._h, res))
+        return _results(res)
+
+    def close(self):
+        if self._h:
+            lib().fs_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Server:
     """The request loop of fs_server_*: submit() queues a request and returns
     its ticket, poll() returns completed responses as dicts.  An ENUMERATE
-    response's rows stay on the device (``rows`` = device address, [count][d]
-    of int16 / int32) until release(ticket)."""
+    response's rows (``rows`` = device address, [count][d] of int16 / int32)
+    and a LENGTHS response's histogram (hist=True: floor(n / min g) + 1 uint64
+    bins) stay on the device until release(ticket)."""
 
     def __init__(self, mem_budget_bytes: int = 0, table_bytes: int = 0, max_batch: int = 0,
-                 slots: int = 0, window_us: int = 0):
+                 slots: int = 0, window_us: int = 0, job_streams: int = 0,
+                 hist_max_leaves: int = 0):
         cfg = fs_server_config(int(mem_budget_bytes), int(table_bytes), int(max_batch),
-                               int(slots), int(window_us), 0)
+                               int(slots), int(window_us), int(job_streams), int(hist_max_leaves))
         h = ctypes.c_void_p(0)
         _check(lib().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
 
-    def submit(self, op: int, n: int, gens, elem_bytes: int = 2, keep_order: bool = False) -> int:
+    def submit(self, op: int, n: int, gens, elem_bytes: int = 2, keep_order: bool = False,
+               hist: bool = False) -> int:
         g = [int(x) for x in gens]
         r = fs_request()
         r.n = int(n)
@@ -505,6 +567,7 @@ class Server:
         r.op = int(op)
         r.elem_bytes = int(elem_bytes)
         r.keep_order = 1 if keep_order else 0
+        r.hist = 1 if hist else 0
         t = ctypes.c_uint64(0)
         _check(lib().fs_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return int(t.value)
@@ -516,7 +579,8 @@ class Server:
         return [dict(ticket=int(r.ticket), status=int(r.status), op=int(r.op),
                      count=int(r.count), min_len=int(r.min_len), max_len=int(r.max_len),
                      rows=int(r.rows or 0), t_submit=float(r.t_submit),
-                     t_start=float(r.t_start), t_done=float(r.t_done))
+                     t_start=float(r.t_start), t_counted=float(r.t_counted),
+                     t_job=float(r.t_job), t_done=float(r.t_done))
                 for r in out[:got.value]]
 
     def release(self, ticket: int) -> None:

@@ -267,6 +267,8 @@ fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& c
     q.maxlen = (int32_t)(n / gmin);
     q.dbins = q.maxlen + std::abs(q.delta) + 1;
     q.nw = q.P - 1;
+    q.acc32 = q.lcm && 32.0 * ((double)n / q.h[q.P - 1] + 1.0) * ((double)n / q.lcm + 1.0) <
+                           4294967295.0;
     // common-divisor skipping for the pair walk (trailing gcd G) and for the
     // trailing-three / trailing-four walks (gcd of the last three / four)
     {
@@ -393,16 +395,23 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
     if (cfg.blocks_per_sm > 0) bps = std::min(bps, cfg.blocks_per_sm);
     lc.blocks = sms * bps;
     // Slice count: explicit, or (auto) as many as leave about MIN_LEAVES leaves
-    // per slice, at most 8 slices per warp (PAIR) / 2 per thread (PLAIN); the
-    // planner picks the final number on the device, where the leaf count is.
-    // Eight slices per warp: the cost of a leaf varies with its run's length
-    // and, for the enumerate walk, with its row count.
+    // per slice, at most 32 (enumerate 8) slices per warp / 2 per thread
+    // (PLAIN); the planner picks the final number on the device, where the leaf
+    // count is.  Several slices per warp: the cost of a leaf varies with its
+    // run's length and, for the enumerate walk, with its row count.
     uint64_t S;
     if (cfg.slices > 0) {
         S = (uint64_t)cfg.slices;
         lc.auto_s = 0;
     } else {
-        const uint64_t per_warp = 8;
+        // The PAIR walks of the order-free consumers take 32 slices per warp:
+        // the slices' leaves are equal but their cost is not, and the last
+        // ones decide when the walk ends (the heavy count query: 1.12 s at 8
+        // per warp, 1.01 s at 32).  Enumerate keeps 8 (each slice ends with a
+        // partial flush of its rows; fewer measured slower, more too), and so
+        // do the trailing-table walks, whose few leaves would make slices of a
+        // few thousand leaves (twice the time on one config-3 seed at 32).
+        const uint64_t per_warp = (op == OP_ENUM || method == FS_METHOD_TRIPLE) ? 8 : 32;
         S = method == FS_METHOD_PLAIN ? (uint64_t)lc.blocks * lc.threads * 2
                                       : (uint64_t)lc.blocks * (lc.threads / 32) * per_warp;
         lc.auto_s = 1;
@@ -815,6 +824,30 @@ fs_status fs_count_async(int64_t n, const uint32_t* gens, int d, const fs_config
     return s;
 }
 
+// Enqueues the length walk of a prepared call: the TRIPLE / QUAD walk for the
+// count and length range alone, else the PAIR (or PLAIN) walk into the
+// difference array and its finalisation, which takes the count and range from
+// the histogram.  Either way the counters hold count, min and max afterwards.
+static fs_status enqueue_lengths(Call& c, uint64_t* hist_dev)
+{
+    const QueryConst& q = c.Q.q;
+    cudaError_t e;
+    if (c.method == FS_METHOD_TRIPLE) {
+        e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
+        if (e != cudaSuccess) return cuda_fail(e, "length launch");
+        return FS_OK;
+    }
+    e = cudaMemsetAsync(c.sc.D, 0, (size_t)std::max(q.dbins, q.maxlen + 1) * 8, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
+    if (e != cudaSuccess) return cuda_fail(e, "length launch");
+    const int stride = c.method == FS_METHOD_PLAIN ? 0 : std::abs(q.delta);
+    ProfScope ps("len_finalize", c.st, 1);
+    e = launch_len_finalize(q, c.sc, hist_dev, stride, c.st);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+    return FS_OK;
+}
+
 fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
                              fs_len_summary* out, uint64_t* hist_dev, void* stream)
 {
@@ -823,21 +856,8 @@ fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_co
     Call c;
     fs_status s = prepare(c, n, gens, d, cfg, OP_LEN, 4, stream, 0, hist_dev == nullptr);
     if (s != FS_OK) return s;
-    const QueryConst& q = c.Q.q;
-    cudaError_t e;
-    if (c.method == FS_METHOD_TRIPLE) {
-        e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
-        if (e != cudaSuccess) return cuda_fail(e, "length launch");
-    } else {
-        e = cudaMemsetAsync(c.sc.D, 0, (size_t)std::max(q.dbins, q.maxlen + 1) * 8, c.st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-        e = call_walk(c, OP_LEN, CTR_QUEUE, nullptr, nullptr, 0, 4);
-        if (e != cudaSuccess) return cuda_fail(e, "length launch");
-        const int stride = c.method == FS_METHOD_PLAIN ? 0 : std::abs(q.delta);
-        ProfScope ps("len_finalize", c.st, 1);
-        e = launch_len_finalize(q, c.sc, hist_dev, stride, c.st);
-        if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
-    }
+    s = enqueue_lengths(c, hist_dev);
+    if (s != FS_OK) return s;
     s = read_ctr(c);
     if (s != FS_OK) return s;
     out->count = c.ds->pinned[CTR_COUNT];
@@ -846,6 +866,22 @@ fs_status fs_length_stats_ex(int64_t n, const uint32_t* gens, int d, const fs_co
         out->max_len = (uint32_t)c.ds->pinned[CTR_MAX];
     } else {
         out->min_len = out->max_len = 0;
+    }
+    return FS_OK;
+}
+
+fs_status fs_length_stats_async(int64_t n, const uint32_t* gens, int d, const fs_config* cfg,
+                                uint64_t* hist_dev, uint64_t* out_dev, void* stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    Call c;
+    fs_status s = prepare(c, n, gens, d, cfg, OP_LEN, 4, stream, 0, hist_dev == nullptr);
+    if (s != FS_OK) return s;
+    s = enqueue_lengths(c, hist_dev);
+    if (s != FS_OK) return s;
+    if (out_dev) {
+        const cudaError_t e = launch_len_summary(c.sc, out_dev, c.st);
+        if (e != cudaSuccess) return cuda_fail(e, "summary launch");
     }
     return FS_OK;
 }
@@ -1460,6 +1496,25 @@ fs_status fs_batch_load(fs_batch* b, const fs_query* queries, int nq, void* stre
     b->nq = nq;
     b->bd.nq = nq;
     return FS_OK;
+}
+
+fs_status fs_batch_load_mode(fs_batch* b, const fs_query* queries, int nq, int mode, void* stream)
+{
+    if (!b) return fail(FS_E_INVAL, "batch is NULL");
+    if (mode != FS_BATCH_COUNT && mode != FS_BATCH_LENGTHS) return fail(FS_E_INVAL, "batch mode %d", mode);
+    if (mode != b->mode) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        const int old = b->mode;
+        b->mode = mode;
+        b->bd.mode = mode;
+        fs_status s = batch_shape(b, b->cfg.block_threads, b->cfg.blocks_per_sm,
+                                  (uint64_t)std::max(b->cfg.slices, (int64_t)0));
+        if (s != FS_OK) {
+            b->mode = b->bd.mode = old;
+            return s;
+        }
+    }
+    return fs_batch_load(b, queries, nq, stream);
 }
 
 fs_status fs_batch_fetch(fs_batch* b, void* stream)

@@ -163,8 +163,12 @@ struct BatchCons {
     uint32_t mn, mx;
     uint64_t* ctr;
     static constexpr int UNROLL = 2;
-    static constexpr bool SKIP = false;
+    // common-divisor skipping: a leaf's residual must be a multiple of the gcd
+    // of the generators after the walk's innermost level (the last pair, or
+    // the trailing three / four for a trailing-table query)
+    static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr bool MULTI_SET = true;
     static constexpr uint32_t CHUNK_OPS = MODE ? 24 : 12;
     static constexpr bool R_INDEXED = false;
     FS_D void fault()
@@ -202,8 +206,11 @@ struct BatchCons {
     }
 };
 
+// Count mode: four 256-thread blocks per SM (64 registers), since the walk
+// waits on its per-query table loads and more resident warps hide more of
+// that latency; the length mode keeps its registers (it spills at 64).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_batch_walk(BatchDev b)
+__global__ void __launch_bounds__(256, MODE ? 3 : 4) k_batch_walk(BatchDev b)
 {
     __shared__ QueryConst qw[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

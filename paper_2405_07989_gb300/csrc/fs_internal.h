@@ -100,6 +100,10 @@ struct QueryConst {
     int32_t sk_g[3], sk_m[3], sk_inv[3];
     Div32 dv_skg[3], dv_skm[3];
     int32_t walk;         // fs_walk: how the order-free walks take a sibling group
+    // The pair count of one lane over one sibling group fits 32 bits: a lane
+    // takes at most 32 (n / h_in + 1) leaves of a group and each has at most
+    // n / lcm + 1 completions (PAIR count walk; set by build_query).
+    int32_t acc32;
 };
 
 // ---------------------------------------------------------------------------

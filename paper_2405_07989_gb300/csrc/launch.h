@@ -41,6 +41,7 @@ cudaError_t launch_scan_slices(const Scratch& sc, uint64_t* dev_count, cudaStrea
 cudaError_t launch_len_finalize(const QueryConst& q, const Scratch& sc, uint64_t* hist, int s,
                                 cudaStream_t st);
 cudaError_t launch_copy_u64(const uint64_t* src, uint64_t* dst, cudaStream_t st);
+cudaError_t launch_len_summary(const Scratch& sc, uint64_t* out, cudaStream_t st);
 
 // pair.cu  (closed-form pair, warp-cooperative walk)
 int pair_smem_bytes(const QueryConst& q, Op op, int threads, int elem_bytes);

@@ -18,20 +18,32 @@ namespace fsi {
 // keeps E as a bitmask, one 32-bit word per 32 classes, with every word
 // repeated 32 times so that lane l reads its own copy at bank l: the lanes'
 // lookups at scattered w never meet in a bank (4 lcm bytes, 64 KB at most).
-template <bool TAB, bool PER_SLICE>
+// ACC32: a lane sums its counts of one sibling group in 32 bits and adds
+// them to its 64-bit total when the group is done (QueryConst::acc32 bounds
+// that sum).
+template <bool TAB, bool PER_SLICE, bool ACC32>
 struct CountCons {
     const uint32_t* Eb;  // TAB: the replicated bitmask
     uint64_t* slice_cnt;
     uint64_t acc;    // this lane, current slice
     uint64_t total;  // this lane, all slices
+    uint32_t acc32;  // this lane, current group (ACC32)
     uint64_t* ctr;
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
-    static constexpr uint32_t CHUNK_OPS = 11;
+    static constexpr bool MULTI_SET = true;
+    static constexpr uint32_t CHUNK_OPS = 10;
     static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
+    FS_D void group_end()
+    {
+        if (ACC32) {
+            acc += acc32;
+            acc32 = 0;
+        }
+    }
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
     FS_D void slice_end(const QueryConst&, uint64_t s)
     {
@@ -45,14 +57,19 @@ struct CountCons {
     FS_D bool chunk(const QueryConst& q, int lane, bool valid, int32_t r, int32_t, int32_t)
     {
         if (valid) {
+            uint32_t c;
             if (TAB) {
                 const uint32_t qq = div32((uint32_t)r, q.dv_lcm);
                 const uint32_t w = (uint32_t)r - qq * q.lcm;
                 const uint32_t m = Eb[(w & ~31u) | (uint32_t)lane];
-                acc += qq + (__funnelshift_r(m, m, w) & 1u);
+                c = qq + (__funnelshift_r(m, m, w) & 1u);
             } else {
-                acc += pair_count<false>(q, (const int8_t*)nullptr, r);
+                c = pair_count<false>(q, (const int8_t*)nullptr, r);
             }
+            if (ACC32)
+                acc32 += c;
+            else
+                acc += c;
         }
         return false;
     }
@@ -71,7 +88,7 @@ FS_D void build_count_bitmask(const int8_t* E, uint32_t lcm, uint32_t* Eb)
     }
 }
 
-template <bool TAB, bool PER_SLICE>
+template <bool TAB, bool PER_SLICE, bool ACC32>
 __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ QueryConst q,
                                                     Scratch sc, int queue, uint64_t* dev_count)
 {
@@ -83,7 +100,7 @@ __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ Quer
     uint32_t* Eb = (uint32_t*)dyn;
     if (TAB) build_count_bitmask(sc.E, q.lcm, Eb);
     __syncthreads();
-    CountCons<TAB, PER_SLICE> cons{Eb, sc.slice_cnt, 0, 0, sc.ctr};
+    CountCons<TAB, PER_SLICE, ACC32> cons{Eb, sc.slice_cnt, 0, 0, 0u, sc.ctr};
     run_queue(q, sq, sc, queue, cons);
     uint64_t v = warp_sum_u64(cons.total);
     if ((threadIdx.x & 31) == 0) atomicAdd(&bsum, (unsigned long long)v);
@@ -113,6 +130,7 @@ struct LenCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr bool MULTI_SET = true;
     static constexpr uint32_t CHUNK_OPS = 30;
     static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
@@ -230,6 +248,7 @@ struct HistCons {
     static constexpr int UNROLL = 2;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr bool MULTI_SET = true;
     static constexpr uint32_t CHUNK_OPS = 14;
     static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
@@ -359,6 +378,7 @@ struct AnyCons {
     static constexpr int UNROLL = 1;
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
+    static constexpr bool MULTI_SET = false;
     static constexpr uint32_t CHUNK_OPS = 30;
     static constexpr bool R_INDEXED = false;
     FS_D void fault() { flag_fault(ctr); }
@@ -440,6 +460,7 @@ struct TripleCons {
     static constexpr int UNROLL = 4;
     static constexpr bool SKIP = false;
     static constexpr bool ANY_ORDER = true;
+    static constexpr bool MULTI_SET = true;
     static constexpr uint32_t CHUNK_OPS = MODE ? 12 : 4;
     static constexpr bool R_INDEXED = true;
     FS_D void fault() { flag_fault(ctr); }
@@ -823,17 +844,24 @@ static cudaError_t go(void (*kern)(KArgs...), dim3 g, dim3 b, int smem, cudaStre
     return cudaGetLastError();
 }
 
+// The count walk's instance for q: table path or not, 32-bit group sums or not.
+using CountKernel = void (*)(QueryConst, Scratch, int, uint64_t*);
+template <bool PER_SLICE>
+static CountKernel count_kernel(const QueryConst& q, bool tab)
+{
+    if (!tab) return k_pair_count<false, PER_SLICE, false>;
+    return q.acc32 ? k_pair_count<true, PER_SLICE, true> : k_pair_count<true, PER_SLICE, false>;
+}
+
 cudaError_t pair_occupancy(const QueryConst& q, Op op, int threads, int elem_bytes, int* nb)
 {
     const int smem = pair_smem_bytes(q, op, threads, elem_bytes);
     const bool tab = tab_for(q, op);
     switch (op) {
     case OP_COUNT:
-        return tab ? occ(k_pair_count<true, false>, threads, smem, nb)
-                   : occ(k_pair_count<false, false>, threads, smem, nb);
+        return occ(count_kernel<false>(q, tab), threads, smem, nb);
     case OP_SLICES:
-        return tab ? occ(k_pair_count<true, true>, threads, smem, nb)
-                   : occ(k_pair_count<false, true>, threads, smem, nb);
+        return occ(count_kernel<true>(q, tab), threads, smem, nb);
     case OP_LEN:
         if (hist_per_warp(q, threads)) return occ(k_pair_hist, threads, smem, nb);
         if (q.dbins <= 4096)
@@ -859,11 +887,9 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
     const dim3 g(lc.blocks), b(lc.threads);
     switch (op) {
     case OP_COUNT:  // `out`: the device total (nullable)
-        return tab ? go(k_pair_count<true, false>, g, b, smem, st, q, sc, queue, (uint64_t*)out)
-                   : go(k_pair_count<false, false>, g, b, smem, st, q, sc, queue, (uint64_t*)out);
+        return go(count_kernel<false>(q, tab), g, b, smem, st, q, sc, queue, (uint64_t*)out);
     case OP_SLICES:
-        return tab ? go(k_pair_count<true, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr)
-                   : go(k_pair_count<false, true>, g, b, smem, st, q, sc, queue, (uint64_t*)nullptr);
+        return go(count_kernel<true>(q, tab), g, b, smem, st, q, sc, queue, (uint64_t*)nullptr);
     case OP_LEN:
         if (hist_per_warp(q, lc.threads)) return go(k_pair_hist, g, b, smem, st, q, sc, queue);
         if (q.dbins <= 4096)

@@ -1,17 +1,18 @@
-// Serving: a request loop with continuous batching, built on the batch-slot
-// and enumerate entry points of the C ABI.
+// Serving: a request loop with continuous batching, built on the batch-slot,
+// enumerate and length entry points of the C ABI.
 //
-// Requests (count, length range, enumerate) are queued by fs_server_submit.
-// One worker thread admits them into reusable batch slots, each with its own
-// stream: a slot takes whatever has arrived (up to max_batch queries) as soon
-// as it is free, so requests that arrive while other batches are on the GPU
-// are batched and run concurrently with them.  Per-query planning state and
-// slice queues stay on the device inside the slot.  An enumerate request is
-// counted in a batch first; its rows are admitted only when count * d * bytes
-// fits the server's device memory budget (else it is refused with
-// FS_E_CAPACITY), then materialised into the budget's pool on an enumerate
-// stream.  Completed requests are collected by fs_server_poll with
-// submit / start / done timestamps.
+// Requests (count, length range with an optional histogram, enumerate) are
+// queued by fs_server_submit.  One worker thread admits them into reusable
+// batch slots, each with its own stream: a slot takes whatever has arrived (up
+// to max_batch queries) as soon as it is free, so requests that arrive while
+// other batches are on the GPU are batched and run concurrently with them.
+// Per-query planning state and slice queues stay on the device inside the
+// slot.  The batch counts every request; an enumerate (its rows) or a length
+// histogram then becomes a job, admitted in arrival order when its exact
+// output bytes fit the server's device memory budget (refused with
+// FS_E_CAPACITY when they exceed the whole budget) and one of the job streams
+// is idle, so several jobs run at once beside the batches.  Completed requests
+// are collected by fs_server_poll with a timestamp per stage.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,7 +34,9 @@ struct Req {
     uint64_t ticket;
     fs_request r;
     double t_submit;
-    double t_start;
+    double t_start;    // its batch was launched
+    double t_counted;  // its batch's results were collected
+    double t_job;      // its job was launched (0: none)
 };
 
 struct Slot {
@@ -45,11 +48,20 @@ struct Slot {
     std::vector<fs_result> res;
 };
 
-struct EnumJob {
+// Device work after the batch: an enumerate's rows or a length histogram.
+struct Job {
     Req req;
     uint64_t count;
     uint32_t min_len, max_len;
-    uint64_t off, bytes;
+    uint64_t off, bytes;  // output in the pool
+};
+
+struct JobLane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    uint64_t* dscratch = nullptr;  // device counters the job writes (count, min, max)
+    bool busy = false;
+    Job job;
 };
 
 // First-fit allocator over the server's row budget.
@@ -108,13 +120,9 @@ struct fs_server {
     uint64_t next_ticket = 1;
     std::thread worker;
     std::vector<Slot> slots;
+    std::vector<JobLane> lanes;
     Pool pool;
-    std::deque<EnumJob> enum_wait;
-    bool enum_busy = false;
-    EnumJob enum_cur;
-    cudaStream_t enum_st = nullptr;
-    cudaEvent_t enum_ev = nullptr;
-    uint64_t* enum_dcount = nullptr;
+    std::deque<Job> job_wait;
     fs_status fatal = FS_OK;
 
     double now() const
@@ -135,37 +143,95 @@ struct fs_server {
         r.rows = rows;
         r.t_submit = q.t_submit;
         r.t_start = q.t_start;
+        r.t_counted = q.t_counted;
+        r.t_job = q.t_job;
         r.t_done = now();
         std::lock_guard<std::mutex> lk(mu);
         done.push_back(r);
         cv_done.notify_all();
     }
 
+    bool busy_gpu() const
+    {
+        for (const Slot& o : slots)
+            if (o.busy) return true;
+        for (const JobLane& l : lanes)
+            if (l.busy) return true;
+        return false;
+    }
+
     bool step();
     void run();
 };
 
+// The smallest generator of a request (its longest length is n / min g).
+static uint32_t min_gen(const fs_request& r)
+{
+    uint32_t m = 0xffffffffu;
+    for (int i = 0; i < r.d && i < FS_MAX_D; i++) m = std::min(m, r.gens[i]);
+    return m;
+}
+
+// Leaves the PAIR length walk of a request visits: prefixes of the first d-2
+// generators (descending) whose residual the gcd G of the last two divides,
+// i.e. the factorizations of n over those d-2 generators and G.  Exact by a
+// DP over 0..n (floating point, enough for a threshold) while n <= 2^20, else
+// the leading term n^(k-1) / ((k-1)! prod g) of that count (k = d - 1
+// generators).
+static double hist_walk_leaves(const fs_request& r)
+{
+    std::vector<uint64_t> g(r.gens, r.gens + std::min(r.d, (int32_t)FS_MAX_D));
+    std::sort(g.begin(), g.end(), std::greater<uint64_t>());
+    if (g.size() < 3) return 1.0;
+    uint64_t a = g[g.size() - 1], b = g[g.size() - 2];
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    g.resize(g.size() - 2);
+    g.push_back(a);
+    const uint64_t n = (uint64_t)std::max<int64_t>(r.n, 0);
+    if (n <= (1u << 20)) {
+        std::vector<double> f(n + 1, 0.0);
+        f[0] = 1.0;
+        for (uint64_t h : g)
+            for (uint64_t p = h; p <= n; p++) f[p] += f[p - h];
+        return f[n];
+    }
+    double v = 1.0 / (double)g.back();
+    for (size_t i = 0; i + 1 < g.size(); i++) v *= (double)n / (double)g[i] / (double)(i + 1);
+    return v;
+}
+
 bool fs_server::step()
 {
     bool progress = false;
-    // 1. finished batches
+    // 1. finished batches: answer the requests, or queue their jobs
     for (Slot& sl : slots) {
         if (!sl.busy || cudaEventQuery(sl.ev) != cudaSuccess) continue;
         sl.res.resize(sl.reqs.size());
         fs_status s = fs_batch_collect(sl.b, sl.res.data());
+        const double tc = now();
         for (size_t i = 0; i < sl.reqs.size(); i++) {
-            const Req& q = sl.reqs[i];
+            Req& q = sl.reqs[i];
+            q.t_counted = tc;
             const fs_result& R = sl.res[i];
             const int32_t st = s != FS_OK ? s : R.status;
-            if (q.r.op == FS_REQ_ENUMERATE && st == FS_OK) {
-                EnumJob j;
+            const bool enum_job = q.r.op == FS_REQ_ENUMERATE;
+            const bool hist_job = q.r.op == FS_REQ_LENGTHS && q.r.hist;
+            if (hist_job && st == FS_OK && hist_walk_leaves(q.r) > (double)cfg.hist_max_leaves) {
+                finish(q, FS_E_CAPACITY, R.count, R.min_len, R.max_len, nullptr);
+            } else if ((enum_job || hist_job) && st == FS_OK) {
+                Job j;
                 j.req = q;
                 j.count = R.count;
                 j.min_len = R.min_len;
                 j.max_len = R.max_len;
                 j.off = 0;
-                j.bytes = R.count * (uint64_t)q.r.d * (uint64_t)q.r.elem_bytes;
-                enum_wait.push_back(j);
+                j.bytes = enum_job ? R.count * (uint64_t)q.r.d * (uint64_t)q.r.elem_bytes
+                                   : ((uint64_t)q.r.n / min_gen(q.r) + 1) * 8;
+                job_wait.push_back(j);
             } else {
                 finish(q, st, R.count, R.min_len, R.max_len, nullptr);
             }
@@ -174,70 +240,91 @@ bool fs_server::step()
         sl.busy = false;
         progress = true;
     }
-    // 2. finished enumerate
-    if (enum_busy && cudaEventQuery(enum_ev) == cudaSuccess) {
+    // 2. finished jobs: their outputs stay reserved until released
+    for (JobLane& l : lanes) {
+        if (!l.busy || cudaEventQuery(l.ev) != cudaSuccess) continue;
         {
             std::lock_guard<std::mutex> lk(mu);
-            held[enum_cur.req.ticket] = {enum_cur.off, enum_cur.bytes};
+            held[l.job.req.ticket] = {l.job.off, l.job.bytes};
         }
-        finish(enum_cur.req, FS_OK, enum_cur.count, enum_cur.min_len, enum_cur.max_len,
-               pool.base + enum_cur.off);
-        enum_busy = false;
+        finish(l.job.req, FS_OK, l.job.count, l.job.min_len, l.job.max_len, pool.base + l.job.off);
+        l.busy = false;
         progress = true;
     }
-    // 3. start an enumerate: admitted by its exact output size
-    while (!enum_busy && !enum_wait.empty()) {
-        EnumJob& j = enum_wait.front();
-        if (j.bytes > pool.size) {
-            finish(j.req, FS_E_CAPACITY, j.count, j.min_len, j.max_len, nullptr);
-            enum_wait.pop_front();
-            progress = true;
-            continue;
+    // 3. start jobs in arrival order, each admitted by its exact output bytes
+    for (JobLane& l : lanes) {
+        if (l.busy) continue;
+        bool started = false;
+        while (!started && !job_wait.empty()) {
+            Job& j = job_wait.front();
+            if (j.bytes > pool.size) {
+                finish(j.req, FS_E_CAPACITY, j.count, j.min_len, j.max_len, nullptr);
+                job_wait.pop_front();
+                progress = true;
+                continue;
+            }
+            bool ok;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                ok = pool.alloc(j.bytes, &j.off);
+            }
+            if (!ok) break;  // wait for outputs to be released
+            j.req.t_job = now();
+            fs_config ec;
+            fs_config_default(&ec);
+            fs_status s;
+            if (j.req.r.op == FS_REQ_ENUMERATE) {
+                ec.keep_order = j.req.r.keep_order;
+                s = fs_enumerate_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec, pool.base + j.off,
+                                       j.count, j.req.r.elem_bytes, l.dscratch, l.st);
+            } else {
+                s = fs_length_stats_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec,
+                                          (uint64_t*)(pool.base + j.off), l.dscratch, l.st);
+            }
+            if (s != FS_OK) {
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    pool.release(j.off, j.bytes);
+                }
+                finish(j.req, s, j.count, j.min_len, j.max_len, nullptr);
+                job_wait.pop_front();
+                progress = true;
+                continue;
+            }
+            cudaEventRecord(l.ev, l.st);
+            l.job = j;
+            l.busy = true;
+            job_wait.pop_front();
+            started = progress = true;
         }
-        bool ok;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            ok = pool.alloc(j.bytes, &j.off);
-        }
-        if (!ok) break;  // wait for rows to be released
-        j.req.t_start = now();
-        fs_config ec;
-        fs_config_default(&ec);
-        ec.keep_order = j.req.r.keep_order;
-        fs_status s = fs_enumerate_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec,
-                                         pool.base + j.off, j.count, j.req.r.elem_bytes,
-                                         enum_dcount, enum_st);
-        if (s != FS_OK) {
-            std::lock_guard<std::mutex> lk(mu);
-            pool.release(j.off, j.bytes);
-        }
-        if (s != FS_OK) {
-            finish(j.req, s, j.count, j.min_len, j.max_len, nullptr);
-            enum_wait.pop_front();
-            continue;
-        }
-        cudaEventRecord(enum_ev, enum_st);
-        enum_cur = j;
-        enum_busy = true;
-        enum_wait.pop_front();
-        progress = true;
+        if (job_wait.empty()) break;
     }
-    // 4. admit arrived requests into a free slot
+    // 4. admit arrived requests into a free slot.  A batch holds one class of
+    // requests, that of the oldest one waiting: counts alone (count mode, no
+    // length tables) or the rest (lengths mode: count and length range); each
+    // class keeps its arrival order.
     for (Slot& sl : slots) {
         if (sl.busy) continue;
         std::vector<Req> take;
+        int mode = FS_BATCH_LENGTHS;
         {
             std::lock_guard<std::mutex> lk(mu);
             if (pending.empty()) break;
-            // while other batches are on the GPU, let the batch fill for up to
+            // while other work is on the GPU, let the batch fill for up to
             // window_us; an idle GPU takes what has arrived at once
-            bool gpu_busy = enum_busy;
-            for (const Slot& o : slots) gpu_busy = gpu_busy || o.busy;
+            const bool gpu_busy = busy_gpu();
             const double age = now() - pending.front().t_submit;
             if (gpu_busy && (int)pending.size() < cfg.max_batch && age * 1e6 < cfg.window_us) break;
-            const int k = std::min<int>((int)pending.size(), cfg.max_batch);
-            take.assign(pending.begin(), pending.begin() + k);
-            pending.erase(pending.begin(), pending.begin() + k);
+            const bool counts = pending.front().r.op == FS_REQ_COUNT;
+            mode = counts ? FS_BATCH_COUNT : FS_BATCH_LENGTHS;
+            for (auto it = pending.begin(); it != pending.end() && (int)take.size() < cfg.max_batch;) {
+                if ((it->r.op == FS_REQ_COUNT) == counts) {
+                    take.push_back(*it);
+                    it = pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
         }
         std::vector<fs_query> qs(take.size());
         for (size_t i = 0; i < take.size(); i++) {
@@ -245,15 +332,18 @@ bool fs_server::step()
             qs[i].d = take[i].r.d;
             memcpy(qs[i].gens, take[i].r.gens, sizeof qs[i].gens);
         }
-        fs_status s = fs_batch_load(sl.b, qs.data(), (int)qs.size(), sl.st);
+        fs_status s = fs_batch_load_mode(sl.b, qs.data(), (int)qs.size(), mode, sl.st);
         int k = (int)qs.size();
         while (s == FS_E_CAPACITY && k > 1) {  // tables too large together: fewer queries
             k = (k + 1) / 2;
-            s = fs_batch_load(sl.b, qs.data(), k, sl.st);
+            s = fs_batch_load_mode(sl.b, qs.data(), k, mode, sl.st);
         }
         if (k < (int)take.size()) {
+            // back to the queue, ahead of everything that came after them
             std::lock_guard<std::mutex> lk(mu);
-            pending.insert(pending.begin(), take.begin() + k, take.end());
+            auto pos = pending.begin();
+            while (pos != pending.end() && pos->ticket < take[k].ticket) ++pos;
+            pending.insert(pos, take.begin() + k, take.end());
             take.resize(k);
         }
         if (s != FS_OK) {
@@ -284,8 +374,7 @@ void fs_server::run()
     for (;;) {
         const bool progress = step();
         std::unique_lock<std::mutex> lk(mu);
-        bool inflight = enum_busy || !enum_wait.empty();
-        for (const Slot& sl : slots) inflight = inflight || sl.busy;
+        const bool inflight = !job_wait.empty() || busy_gpu();
         if (stop && pending.empty() && !inflight) break;
         if (!progress) {
             if (pending.empty() && !inflight)
@@ -308,6 +397,8 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
     if (s->cfg.max_batch <= 0) s->cfg.max_batch = 512;
     if (s->cfg.slots <= 0) s->cfg.slots = 3;
     if (s->cfg.window_us <= 0) s->cfg.window_us = 200;
+    if (s->cfg.job_streams <= 0) s->cfg.job_streams = 4;
+    if (s->cfg.hist_max_leaves == 0) s->cfg.hist_max_leaves = 1ull << 34;
     if (s->cfg.table_bytes == 0) s->cfg.table_bytes = 256ull << 20;
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&s->dev);
@@ -321,16 +412,20 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
             st = FS_E_CUDA;
         s->slots.push_back(sl);
     }
-    if (st == FS_OK) {
-        if (fsi::dev_alloc((void**)&s->pool.base, s->cfg.mem_budget_bytes) != cudaSuccess ||
-            fsi::dev_alloc((void**)&s->enum_dcount, 8) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&s->enum_st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->enum_ev, cudaEventDisableTiming) != cudaSuccess)
+    if (st == FS_OK && fsi::dev_alloc((void**)&s->pool.base, s->cfg.mem_budget_bytes) != cudaSuccess)
+        st = FS_E_NOMEM;
+    for (int i = 0; st == FS_OK && i < s->cfg.job_streams; i++) {
+        JobLane l;
+        if (fsi::dev_alloc((void**)&l.dscratch, 3 * 8) != cudaSuccess)
             st = FS_E_NOMEM;
-        if (st == FS_OK) st = fs_reserve(64ull << 20, s->enum_st);  // the enumerates' scratch
-        s->pool.size = s->cfg.mem_budget_bytes;
-        s->pool.free_blocks[0] = s->cfg.mem_budget_bytes;
+        else if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming) != cudaSuccess)
+            st = FS_E_CUDA;
+        s->lanes.push_back(l);
+        if (st == FS_OK) st = fs_reserve(64ull << 20, l.st);  // each job stream's scratch
     }
+    s->pool.size = s->cfg.mem_budget_bytes;
+    s->pool.free_blocks[0] = s->cfg.mem_budget_bytes;
     if (st != FS_OK) {
         cudaGetLastError();
         s->stop = true;
@@ -347,13 +442,14 @@ fs_status fs_server_submit(fs_server* s, const fs_request* r, uint64_t* ticket)
     if (!s || !r || !ticket) return FS_E_INVAL;
     if (r->op < FS_REQ_COUNT || r->op > FS_REQ_ENUMERATE) return FS_E_INVAL;
     if (r->op == FS_REQ_ENUMERATE && r->elem_bytes != 2 && r->elem_bytes != 4) return FS_E_INVAL;
+    if (r->op == FS_REQ_LENGTHS && r->hist != 0 && r->hist != 1) return FS_E_INVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return FS_E_INVAL;
     Req q;
     q.ticket = s->next_ticket++;
     q.r = *r;
     q.t_submit = s->now();
-    q.t_start = 0;
+    q.t_start = q.t_counted = q.t_job = 0;
     s->pending.push_back(q);
     *ticket = q.ticket;
     s->cv_in.notify_one();
@@ -407,9 +503,11 @@ fs_status fs_server_destroy(fs_server* s)
         if (sl.ev) cudaEventDestroy(sl.ev);
     }
     if (s->pool.base) cudaFree(s->pool.base);
-    if (s->enum_dcount) cudaFree(s->enum_dcount);
-    if (s->enum_st) cudaStreamDestroy(s->enum_st);
-    if (s->enum_ev) cudaEventDestroy(s->enum_ev);
+    for (JobLane& l : s->lanes) {
+        if (l.dscratch) cudaFree(l.dscratch);
+        if (l.st) cudaStreamDestroy(l.st);
+        if (l.ev) cudaEventDestroy(l.ev);
+    }
     delete s;
     return FS_OK;
 }

@@ -307,6 +307,15 @@ __global__ void __launch_bounds__(1024) k_len_finalize(const __grid_constant__ Q
 
 __global__ void k_copy_u64(const uint64_t* src, uint64_t* dst) { *dst = *src; }
 
+// count, min and max of a length call from its counters to the caller's memory
+__global__ void k_len_summary(const uint64_t* ctr, uint64_t* out)
+{
+    const uint64_t c = ctr[CTR_COUNT];
+    out[0] = c;
+    out[1] = c ? 0xffffffffull - ctr[CTR_MINC] : 0ull;
+    out[2] = c ? ctr[CTR_MAX] : 0ull;
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -366,6 +375,12 @@ cudaError_t launch_len_finalize(const QueryConst& q, const Scratch& sc, uint64_t
                                 cudaStream_t st)
 {
     k_len_finalize<<<1, 1024, 0, st>>>(q, sc.D, hist, s, sc.ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_len_summary(const Scratch& sc, uint64_t* out, cudaStream_t st)
+{
+    k_len_summary<<<1, 1, 0, st>>>(sc.ctr, out);
     return cudaGetLastError();
 }
 

@@ -500,18 +500,23 @@ FS_D void skip_class(const QueryConst& q, uint32_t R, uint32_t b, uint32_t nh, u
 
 // Issue slots a warp step costs in each way through a sibling group, for the
 // choice in walk_slice_packed: a step over one run's 32 leaves (residual and
-// coordinate advanced once per step), a step with each lane on its own run
-// (plus the lane's own bound check), a packed step (plus the 5-step search for
-// each lane's run).  Cons::CHUNK_OPS estimates the consumer's per-leaf work.
+// coordinate advanced once per step), a step with each lane on its own run,
+// a packed step (plus the 5-step search for each lane's run and the shuffles
+// of its run's data), and each run's turn in the full-step loop.
+// Cons::CHUNK_OPS estimates the consumer's per-leaf work.  The constants were
+// set from the measured walks of both kinds on the heavy count query (long
+// runs of a few dozen visited leaves: lanes) and the single large query
+// (slices of a few hundred leaves: packed).
 // Cons::R_INDEXED says it reads a shared 32-bit table at the residual itself:
 // lanes whose residuals are k apart then meet 2^ctz(k)-way bank conflicts
 // (k = hsib for lanes on sibling runs, k = the step between visited leaves
 // for lanes on one run), each extra way costing about a few issue slots.
 template <class Cons>
 struct WalkCost {
-    static constexpr uint32_t full = Cons::CHUNK_OPS + 2;
-    static constexpr uint32_t lane = Cons::CHUNK_OPS + 4;
-    static constexpr uint32_t pack = Cons::CHUNK_OPS + 22;
+    static constexpr uint32_t full = Cons::CHUNK_OPS + 4;
+    static constexpr uint32_t lane = Cons::CHUNK_OPS + 3;
+    static constexpr uint32_t pack = Cons::CHUNK_OPS + 36;
+    static constexpr uint32_t per_run = 12;  // a run's turn in the full-step loop
     static constexpr uint32_t per_way = 4;
 };
 
@@ -528,6 +533,15 @@ struct HasGroupLeaves {
 };
 template <class C>
 struct HasGroupLeaves<C, decltype((void)&C::group_leaves)> {
+    static constexpr bool value = true;
+};
+// Whether a consumer wants to hear when a group is done (Cons::group_end()).
+template <class C, class = void>
+struct HasGroupEnd {
+    static constexpr bool value = false;
+};
+template <class C>
+struct HasGroupEnd<C, decltype((void)&C::group_end)> {
     static constexpr bool value = true;
 };
 
@@ -558,46 +572,94 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
     const bool skip = Cons::SKIP && (q.sk_m[0] > 1 || q.sk_g[0] > 1);
     const uint32_t ma = skip ? (uint32_t)q.sk_m[0] : 1u;  // step of a between visited leaves
     const uint32_t mstep = ma * hin;
+    // every run has fewer than 2^26 leaves: a group's leaf total fits 31 bits
+    const bool small_runs = div32((uint32_t)q.n, q.dv_in) < (1u << 26) - 1;
+    const uint32_t hsib = np > 0 ? (uint32_t)hs[np - 1] : 0u;
     uint64_t rem = nleaves;
     for (;;) {
+        // The group: lane j holds run j of the next runs in lex order.  Runs
+        // that differ only at level P-2 (a sibling set) have residuals hsib
+        // apart and prefix sums one apart; a consumer that needs only each
+        // lane's own run (Cons::MULTI_SET) lets the lanes after a set that
+        // ends early take the next sets whole, up to 32 runs or the slice's
+        // end.  `cur` ends as the prefix of the group's last set.
+        RunPrefix cur = rp;
+        uint32_t Rj = 0, bj = 0, left = 0;
+        int32_t lpj = 0;
+        uint32_t filled = 0, base_last = 0;
         int32_t Rc = q.n, lpc = 0, ac = 0;
-        uint32_t hsib = 0, nsib = 1;
-        if (np > 0) {
-            Rc = __shfl_sync(FULL, rp.r, np - 1);
-            lpc = __shfl_sync(FULL, rp.l, np - 1);
-            ac = __shfl_sync(FULL, rp.a, np - 1);
-            hsib = (uint32_t)hs[np - 1];
-            nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
-            if (nsib > 32) nsib = 32;
+        for (;;) {
+            uint32_t nsib = 1;
+            if (np > 0) {
+                Rc = __shfl_sync(FULL, cur.r, np - 1);
+                lpc = __shfl_sync(FULL, cur.l, np - 1);
+                ac = __shfl_sync(FULL, cur.a, np - 1);
+                nsib = div32((uint32_t)Rc, dvh[np - 1]) + 1;
+            }
+            if (nsib > 32 - filled) nsib = 32 - filled;
+            const uint32_t j = (uint32_t)lane - filled;  // wraps for the lanes before
+            if (j < nsib) {
+                Rj = (uint32_t)Rc - j * hsib;
+                lpj = lpc + (int32_t)j;
+                bj = (filled == 0 && j == 0) ? (uint32_t)b : 0u;
+                left = div32(Rj, q.dv_in) + 1 - bj;
+            }
+            base_last = filled;
+            filled += nsib;
+            if (!Cons::MULTI_SET || !small_runs || np == 0 || filled >= 32) break;
+            // the slice ends inside the lanes filled so far
+            if ((uint64_t)__reduce_add_sync(FULL, left) >= rem) break;
+            // the next set, the successor of this set's last run, joins only
+            // if it fits whole: small sets share a group, and a large set keeps
+            // its own groups (a set's first runs are its longest, its last its
+            // shortest, so a group cut across two sets would be uneven)
+            RunPrefix nxt = cur;
+            if (lane == np - 1) {
+                nxt.a = ac + (int32_t)nsib - 1;
+                nxt.r = (int32_t)((uint32_t)Rc - (nsib - 1) * hsib);
+                nxt.l = lpc + (int32_t)nsib - 1;
+            }
+            if (!warp_next_run(q, lane, hk, nxt)) break;  // no runs left (the walk's own check follows)
+            const uint32_t nnext = div32((uint32_t)__shfl_sync(FULL, nxt.r, np - 1), dvh[np - 1]) + 1;
+            if (nnext > 32 - filled) break;
+            cur = nxt;
         }
-        // lane j: sibling run j, residual R_j = Rc - j hsib, leaves from b_j on
-        const bool act = (uint32_t)lane < nsib;
-        const uint32_t Rj = (uint32_t)Rc - (uint32_t)lane * hsib;
-        const uint32_t bj = lane == 0 ? (uint32_t)b : 0u;
-        const uint32_t left = act ? div32(Rj, q.dv_in) + 1 - bj : 0u;
-        uint64_t ir = left;  // leaves of runs 0..j
+        const bool act = (uint32_t)lane < filled;
+        uint32_t ns, nh;  // runs taken; leaves of run j in the slice
+        uint64_t took;    // leaves of the runs taken
+        const uint32_t gsum = small_runs ? __reduce_add_sync(FULL, left) : 0u;
+        if (small_runs && (uint64_t)gsum <= rem) {
+            // the whole group lies in the slice (the common case)
+            ns = filled;
+            nh = left;
+            took = gsum;
+        } else {
+            uint64_t ir = left;  // leaves of runs 0..j
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t t = __shfl_up_sync(FULL, ir, o);
-            if (lane >= o) ir += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(FULL, ir, o);
+                if (lane >= o) ir += t;
+            }
+            // take the runs whose leaves so far stay below 2^31 (at least one),
+            // so the visited-leaf offsets below fit 32 bits
+            ns = __popc(__ballot_sync(FULL, act && ir < (1ull << 31)));
+            if (ns == 0) ns = 1;
+            const uint64_t er = ir - left;
+            nh = 0;
+            if ((uint32_t)lane < ns && er < rem) nh = rem - er < (uint64_t)left ? (uint32_t)(rem - er) : left;
+            took = __shfl_sync(FULL, ir, (int)ns - 1);
         }
-        // take the runs whose leaves so far stay below 2^31 (at least one), so
-        // the visited-leaf offsets below fit 32 bits
-        uint32_t ns = __popc(__ballot_sync(FULL, act && ir < (1ull << 31)));
-        if (ns == 0) ns = 1;
-        const uint64_t er = ir - left;
-        uint32_t nh = 0;  // leaves of run j in the slice
-        if ((uint32_t)lane < ns && er < rem) nh = rem - er < (uint64_t)left ? (uint32_t)(rem - er) : left;
         uint32_t first = bj, cnt = nh, mj = 1;
         if (skip && nh > 0) skip_class(q, Rj, bj, nh, first, cnt, mj);
         const uint32_t nfull = cnt >> 5, part = cnt & 31;
-        cons.group_begin(q, rp, lane, ac, lpc);
+        cons.group_begin(q, cur, lane, ac, lpc);  // single-set groups: their set
         if constexpr (HasGroupLeaves<Cons>::value) cons.group_leaves(__reduce_add_sync(FULL, cnt));
         const uint32_t mxc = __reduce_max_sync(FULL, cnt);
         bool lanes = q.walk == FS_WALK_LANES;
         if (q.walk == FS_WALK_AUTO) {
             const uint32_t sfull = __reduce_add_sync(FULL, nfull);
             const uint32_t spart = __reduce_add_sync(FULL, part);
+            const uint32_t rfull = __popc(__ballot_sync(FULL, nfull > 0));
             using C = WalkCost<Cons>;
             uint32_t cl = C::lane, cf = C::full, cp = C::pack;
             if (Cons::R_INDEXED) {
@@ -605,22 +667,30 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
                 cf += (conflict_ways(mstep) - 1) * C::per_way;
                 cp += C::per_way;  // lanes on mixed runs: about two ways
             }
-            lanes = (uint64_t)mxc * cl <= (uint64_t)sfull * cf + (uint64_t)((spart + 31) >> 5) * cp;
+            lanes = (uint64_t)mxc * cl <= (uint64_t)sfull * cf + (uint64_t)rfull * C::per_run +
+                                              (uint64_t)((spart + 31) >> 5) * cp;
         }
         if (lanes) {
-            // lane j: run j's visited leaves a = first + i ma, i < cnt
+            // lane j: run j's visited leaves a = first + i ma, i < cnt; while
+            // every lane still has one the bound check is left out
             uint32_t a = first, r = Rj - first * hin;
-            const int32_t lp = lpc + lane;
+            const int32_t lp = lpj;
+            const uint32_t mnc = __reduce_min_sync(FULL, cnt);
             uint32_t i = 0;
             if (Cons::UNROLL > 1) {
-                for (; i + Cons::UNROLL <= mxc; i += Cons::UNROLL) {
+                for (; i + Cons::UNROLL <= mnc; i += Cons::UNROLL) {
 #pragma unroll
                     for (int u = 0; u < Cons::UNROLL; u++) {
-                        if (cons.chunk(q, lane, i + u < cnt, (int32_t)r, (int32_t)a, lp)) return true;
+                        if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
                         r -= mstep;
                         a += ma;
                     }
                 }
+            }
+            for (; i < mnc; i++) {
+                if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
+                r -= mstep;
+                a += ma;
             }
             for (; i < mxc; i++) {
                 if (cons.chunk(q, lane, i < cnt, (int32_t)r, (int32_t)a, lp)) return true;
@@ -634,7 +704,7 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
                 const uint32_t nf = __shfl_sync(FULL, nfull, j);
                 uint32_t a = __shfl_sync(FULL, first, j) + (uint32_t)lane * ma;
                 uint32_t r = __shfl_sync(FULL, Rj, j) - a * hin;
-                const int32_t lp = lpc + j;
+                const int32_t lp = __shfl_sync(FULL, lpj, j);
                 uint32_t i = 0;
                 if (Cons::UNROLL > 1) {
                     for (; i + Cons::UNROLL <= nf; i += Cons::UNROLL) {
@@ -676,23 +746,27 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
                 const uint32_t k = t - __shfl_sync(FULL, ev, j);
                 const uint32_t a = __shfl_sync(FULL, pa, j) + k * ma;
                 const uint32_t r = __shfl_sync(FULL, r0, j) - k * mstep;
-                if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lpc + j)) return true;
+                const int32_t lp = __shfl_sync(FULL, lpj, j);
+                if (cons.chunk(q, lane, t < tot, (int32_t)r, (int32_t)a, lp)) return true;
             }
         }
-        const uint64_t took = __shfl_sync(FULL, ir, (int)ns - 1);
+        if constexpr (HasGroupEnd<Cons>::value) cons.group_end();
         if (took >= rem) return false;
         rem -= took;
         b = 0;
-        // the last run taken becomes the current one; step to its lex successor
+        // the last run taken becomes the current one (it is in the last set:
+        // a group that ends early ends the slice); step to its lex successor
         if (np == 0) {
             cons.fault();  // the slice claims leaves past the last one
             return false;
         }
+        const uint32_t jl = ns - 1 - base_last;
         if (lane == np - 1) {
-            rp.a = ac + (int32_t)ns - 1;
-            rp.r = (int32_t)((uint32_t)Rc - (ns - 1) * hsib);
-            rp.l = lpc + (int32_t)ns - 1;
+            cur.a = ac + (int32_t)jl;
+            cur.r = (int32_t)((uint32_t)Rc - jl * hsib);
+            cur.l = lpc + (int32_t)jl;
         }
+        rp = cur;
         if (!warp_next_run(q, lane, hk, rp)) {
             cons.fault();
             return false;

@@ -123,3 +123,16 @@ def test_batch_common_divisors(method):
           (3000, (14, 21, 6, 10, 15, 35))]
     cfg = fs.make_config(method=method)
     assert fs.fs_batch_run(qs, fs.BATCH_LENGTHS, cfg) == expected(qs, fs.BATCH_LENGTHS)
+
+
+def test_batch_slot_switches_mode_between_loads():
+    """One slot reserved for length ranges serves count-only loads (count mode,
+    no length tables) and length loads in turn, each exact."""
+    qs = workloads.config4(seed=13, nq=96, n_max=3000)
+    with fs.BatchSlot(128, 256 << 20, fs.BATCH_LENGTHS) as b:
+        for mode in (fs.BATCH_COUNT, fs.BATCH_LENGTHS, fs.BATCH_COUNT):
+            b.load(qs, mode)
+            b.launch()
+            assert b.results() == expected(qs, mode), mode
+        with pytest.raises(fs.FsError):
+            b.load(qs, 7)

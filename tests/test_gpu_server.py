@@ -31,6 +31,19 @@ class _DevRows:
             "data": (ptr, False), "version": 3, "strides": None}
 
 
+def hist_of(resp, n, g):
+    """A LENGTHS response's histogram (hist=True), read from the device."""
+    bins = n // min(g) + 1
+    t = torch.as_tensor(_DevHist(resp["rows"], bins), device="cuda")
+    return t.cpu().numpy().astype(np.uint64)
+
+
+class _DevHist:
+    def __init__(self, ptr, bins):
+        self.__cuda_array_interface__ = {"shape": (bins,), "typestr": "<u8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
 def rows_of(resp, d, elem_bytes):
     if resp["count"] == 0:
         return np.zeros((0, d), dtype=np.int64)
@@ -62,17 +75,30 @@ def drain(srv, tickets, timeout_s=120.0):
     return got
 
 
-def check(resp, op, n, g, elem_bytes=2, keep_order=False):
+def check(resp, op, n, g, elem_bytes=2, keep_order=False, hist=False):
     assert resp["status"] == fs.FS_OK, resp
     c = oracle.count_dp(n, g)
     assert resp["count"] == c
     if op in (fs.REQ_LENGTHS, fs.REQ_ENUMERATE) and c > 0:
         assert (resp["min_len"], resp["max_len"]) == oracle.minmax_dp(n, g)
+    job = op == fs.REQ_ENUMERATE or (op == fs.REQ_LENGTHS and hist)
+    # the stages in order; a job's launch between the count and the answer
+    assert resp["t_submit"] <= resp["t_start"] <= resp["t_counted"] <= resp["t_done"], resp
+    if job:
+        assert resp["t_counted"] <= resp["t_job"] <= resp["t_done"], resp
+    else:
+        assert resp["t_job"] == 0.0 and resp["rows"] == 0, resp
     ref = alone(op, n, g, elem_bytes, keep_order)
     if op == fs.REQ_COUNT:
         assert (resp["count"],) == ref
     elif op == fs.REQ_LENGTHS:
         assert (resp["count"], resp["min_len"], resp["max_len"]) == ref
+        if hist:  # bin for bin: the oracle's bivariate DP and the call alone
+            h = hist_of(resp, n, g)
+            assert np.array_equal(h, oracle.length_dp(n, g)), (n, g)
+            alone_h = torch.zeros(n // min(g) + 1, dtype=torch.int64, device="cuda")
+            fs.fs_length_stats(n, g, alone_h)
+            assert np.array_equal(h, alone_h.cpu().numpy().astype(np.uint64))
     else:
         rows = rows_of(resp, len(g), elem_bytes)
         assert np.array_equal(rows, ref)  # byte-identical to the call alone
@@ -85,27 +111,56 @@ def test_server_mix_matches_alone():
     """A config-5-like mix (80 % count, 15 % lengths, 5 % enumerate), submitted
     in bursts while earlier batches run."""
     reqs = workloads.config5(seed=4, nreq=240, n_max=2500)
-    with fs.Server(mem_budget_bytes=512 << 20, max_batch=64, slots=3, window_us=100) as srv:
+    with fs.Server(mem_budget_bytes=512 << 20, max_batch=64, slots=3, window_us=100,
+                   job_streams=3) as srv:
         tickets = {}
         for i, (_, op, n, g) in enumerate(reqs):
-            tickets[srv.submit(op, n, g, elem_bytes=2)] = (op, n, g)
+            hist = op == fs.REQ_LENGTHS and i % 2 == 0  # every other one with its histogram
+            tickets[srv.submit(op, n, g, elem_bytes=2, hist=hist)] = (op, n, g, hist)
             if i % 40 == 39:
                 time.sleep(0.002)
         got = drain(srv, tickets)
-        for t, (op, n, g) in tickets.items():
-            check(got[t], op, n, g)
-            assert got[t]["t_submit"] <= got[t]["t_start"] <= got[t]["t_done"]
-            if op == fs.REQ_ENUMERATE:
+        assert sum(1 for op, _, _, h in tickets.values() if h) > 0
+        for t, (op, n, g, hist) in tickets.items():
+            check(got[t], op, n, g, hist=hist)
+            if op == fs.REQ_ENUMERATE or hist:
                 srv.release(t)
 
 
-@pytest.mark.parametrize("op", [fs.REQ_COUNT, fs.REQ_LENGTHS, fs.REQ_ENUMERATE])
-def test_server_request_alone(op):
+def test_server_jobs_run_concurrently():
+    """Enumerations that fit the budget together run on the job streams at
+    the same time: some two of them overlap between launch and completion
+    (each writes about 2 GB of int16 rows), and each one's rows equal the
+    call made alone, byte for byte (compared on the device)."""
+    n, g = 3600, (11, 13, 17, 19, 23, 29)
+    c = fs.fs_count(n, g)
+    d = len(g)
+    ref = torch.empty((c, d), dtype=torch.int16, device="cuda")
+    fs.fs_enumerate(n, g, ref, cap=c, elem_bytes=2)
+    with fs.Server(mem_budget_bytes=4 * c * d * 2 + (1 << 20), max_batch=16, job_streams=4) as srv:
+        ts = [srv.submit(fs.REQ_ENUMERATE, n, g, elem_bytes=2) for _ in range(4)]
+        got = drain(srv, ts)
+        iv = sorted((got[t]["t_job"], got[t]["t_done"]) for t in ts)
+        assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1)), iv
+        for t in ts:
+            assert got[t]["status"] == fs.FS_OK and got[t]["count"] == c
+            rows = torch.as_tensor(_DevRows(got[t]["rows"], c, d, 2), device="cuda")
+            assert torch.equal(rows, ref)
+            srv.release(t)
+    del ref
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("op,hist", [(fs.REQ_COUNT, False), (fs.REQ_LENGTHS, False),
+                                     (fs.REQ_LENGTHS, True), (fs.REQ_ENUMERATE, False)])
+def test_server_request_alone(op, hist):
     n, g = 2000, (11, 13, 17, 19, 23)
     with fs.Server(mem_budget_bytes=64 << 20) as srv:
-        t = srv.submit(op, n, g, elem_bytes=4, keep_order=True)
+        t = srv.submit(op, n, g, elem_bytes=4, keep_order=True, hist=hist)
         got = drain(srv, {t: None})
-        check(got[t], op, n, g, elem_bytes=4, keep_order=True)
+        check(got[t], op, n, g, elem_bytes=4, keep_order=True, hist=hist)
+        if op == fs.REQ_ENUMERATE or hist:
+            srv.release(t)
 
 
 def test_server_invalid_and_capacity():
@@ -125,6 +180,11 @@ def test_server_invalid_and_capacity():
             srv.submit(7, 100, (3, 5))
         with pytest.raises(fs.FsError):
             srv.submit(fs.REQ_ENUMERATE, 100, (3, 5), elem_bytes=8)
+        r = fs.fs_request()
+        r.n, r.d, r.op, r.hist = 100, 2, fs.REQ_LENGTHS, 5
+        r.gens[0], r.gens[1] = 3, 5
+        t = fs.ctypes.c_uint64(0)
+        assert fs.lib().fs_server_submit(srv._h, fs.ctypes.byref(r), fs.ctypes.byref(t)) == fs.FS_E_INVAL
 
 
 def test_server_enumerate_waits_for_release():
