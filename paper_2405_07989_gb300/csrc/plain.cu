@@ -47,15 +47,17 @@ FS_D bool next_candidate(const QueryConst& q, const SmemQP& sq, int32_t (&a)[MAX
     for (int k = 0; k < MAXD - 1; k++)
         if (k < D - 1 && a[k] > 0) piv = k;
     if (piv < 0) return false;
-    // lower the pivot, clear the rest (only the final coordinate can be
-    // nonzero right of the pivot), and sum phi of what is left
-    int64_t phi = 0;
+    // lower the pivot and clear the rest: right of the pivot only the final
+    // coordinate can be nonzero
 #pragma unroll
     for (int k = 0; k < MAXD; k++) {
+        if (k == D - 1) a[k] = 0;
         if (k == piv) a[k] -= 1;
-        if (k > piv) a[k] = 0;
-        if (k < D) phi += (int64_t)a[k] * sq.h[k];
     }
+    int64_t phi = 0;
+#pragma unroll
+    for (int k = 0; k < MAXD; k++)
+        if (k < D) phi += (int64_t)a[k] * sq.h[k];
     const int32_t rest = q.n - (int32_t)phi;
     const int32_t hn = sq.h[piv + 1];
     int32_t m = (int32_t)div32((uint32_t)rest, sq.dvh[piv + 1]);
