@@ -902,14 +902,20 @@ def run_profile_case(args):
     larger than L2); "count" / "count_triple" / "count_quad": the heavy
     count-only query's generators at --profile-n through the PAIR walk or the
     trailing-three / trailing-four tables; "lengths": the same generators'
-    count, length range and histogram (PAIR walk); "batch": the first --profile-n
+    count, length range and histogram (PAIR walk); "batch5": the first
+    --profile-n queries of the serving workload in one batch (--profile-mode);
+    "batch": the first --profile-n
     queries of the batched workload, count mode."""
     import torch
     import paper_2405_07989_gb300 as fs
     from paper_2405_07989_gb300 import workloads
-    if args.profile_case == "batch":
-        qs = workloads.config4(0, nq=args.profile_n)
-        with fs.Batch(qs, fs.BATCH_COUNT) as b:
+    if args.profile_case in ("batch", "batch5"):
+        if args.profile_case == "batch":
+            qs = workloads.config4(0, nq=args.profile_n)
+        else:
+            qs = [(n, g) for (_, op, n, g) in workloads.config5(0, args.profile_n, 1000.0, 20000)]
+        mode = fs.BATCH_LENGTHS if args.profile_mode == "lengths" else fs.BATCH_COUNT
+        with fs.Batch(qs, mode) as b:
             for _ in range(args.steps):
                 b.launch()
             res = b.results()
@@ -962,12 +968,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the heavy count-only query measurements")
     ap.add_argument("--profile-case",
-                    choices=["enum", "count", "count_triple", "count_quad", "lengths", "batch"],
+                    choices=["enum", "count", "count_triple", "count_quad", "lengths", "batch",
+                             "batch5"],
                     default=None,
                     help="run only a small case of the same kernels (for ncu)")
     ap.add_argument("--profile-n", type=int, default=2000)
     ap.add_argument("--profile-walk", choices=["auto", "packed", "lanes"], default="auto",
                     help="profile cases: how the order-free walks take a sibling group")
+    ap.add_argument("--profile-mode", choices=["count", "lengths"], default="count",
+                    help="batch profile cases: count only, or count and length range")
     ap.add_argument("--serve-rate", type=float, default=1000.0,
                     help="serving extras: Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=2000)
