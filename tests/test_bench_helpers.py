@@ -41,3 +41,57 @@ def test_kernel_hash_follows_the_include_closure(tree):
     _edit(csrc / "walk.cuh", "namespace fsi {", "namespace fsi {\nconstexpr int probe_constant = 1;")
     assert bench.kernel_source_sha("pair_enum") != h0
 
+
+
+def test_recorded_counters_apply_only_to_their_sources(tree, monkeypatch):
+    """The recorded traffic and instruction counts are used while the hash of the
+    kernel's sources matches, and ignored (None) once the kernel changes."""
+    prof = tree / "profiles"
+    prof.mkdir()
+    sha = bench.kernel_source_sha("pair_count")
+    (prof / "count_inst.json").write_text(
+        '{"pair_count": {"source_sha": "%s", "alu_warp_inst": 10, "fma_warp_inst": 6,'
+        ' "warp_inst": 20, "n": 5, "gens": [1, 2, 3]}}' % sha)
+    assert bench.recorded_instructions("pair_count")["warp_inst"] == 20
+    _edit(tree / "paper_2405_07989_gb300" / "csrc" / "pair.cu", "namespace fsi {",
+          "namespace fsi {\nconstexpr int probe_constant = 2;")
+    assert bench.recorded_instructions("pair_count") is None
+    assert bench.recorded_instructions("no_such_kernel") is None
+
+
+class _FakeFs:
+    """fs_count over a brute-force count, for the leaf formulas on the host."""
+
+    @staticmethod
+    def fs_count(n, gens):
+        def rec(i, rest):
+            if i == len(gens) - 1:
+                return 1 if rest % gens[i] == 0 else 0
+            return sum(rec(i + 1, rest - k * gens[i]) for k in range(rest // gens[i] + 1))
+        return rec(0, n)
+
+
+def test_count_roofline_units_are_the_walk_leaves():
+    """The PAIR walk visits the prefixes of the first d-2 generators (descending)
+    whose residual the last pair's gcd divides; the QUAD walk every prefix of
+    the first d-4.  Checked against direct enumeration of those prefixes."""
+    import itertools
+    import math
+    n, g = 60, (12, 10, 9, 7, 6, 4)
+    w = sorted(g, reverse=True)
+    G = math.gcd(w[-1], w[-2])
+    pre = w[:-2]
+    direct = 0
+    for a in itertools.product(*[range(n // h + 1) for h in pre]):
+        phi = sum(x * h for x, h in zip(a, pre))
+        if phi <= n and (n - phi) % G == 0:
+            direct += 1
+    assert bench.visited_leaves(_FakeFs, n, g) == direct
+    pre4 = w[:-4]
+    direct4 = sum(1 for a in itertools.product(*[range(n // h + 1) for h in pre4])
+                  if sum(x * h for x, h in zip(a, pre4)) <= n)
+    assert bench.quad_leaves(_FakeFs, n, g) == direct4
+    rates = {"add": 1e12}
+    r = bench.count_roofline(_FakeFs, n, g, 2.0, rates)
+    assert r["leaves_resolved"] == direct and r["frac"] is None
+    assert abs(r["useful_frac"] - direct * bench.COUNT_OPS_PER_LEAF / 2e-3 / 1e12) < 1e-12

@@ -258,3 +258,20 @@ def test_server_serving_workload_full():
         assert r["status"] == fs.FS_OK, (op, n, g, r["status"])
         if op in (fs.REQ_LENGTHS, fs.REQ_ENUMERATE) and c > 0:
             assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(n, g), (op, n, g)
+
+
+def test_server_histogram_work_bound():
+    """A histogram whose PAIR walk would visit more than hist_max_leaves leaves is
+    refused with FS_E_CAPACITY, its count and length range still exact; one
+    under the bound is served with its histogram."""
+    big, small = (2000, (11, 13, 17, 19, 23)), (300, (5, 7, 11, 13))
+    with fs.Server(mem_budget_bytes=64 << 20, hist_max_leaves=2000) as srv:
+        tb = srv.submit(fs.REQ_LENGTHS, *big, hist=True)
+        ts = srv.submit(fs.REQ_LENGTHS, *small, hist=True)
+        got = drain(srv, [tb, ts])
+        r = got[tb]
+        assert r["status"] == fs.FS_E_CAPACITY and r["rows"] == 0
+        assert r["count"] == oracle.count_dp(*big)
+        assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(*big)
+        check(got[ts], fs.REQ_LENGTHS, *small, hist=True)
+        srv.release(ts)
