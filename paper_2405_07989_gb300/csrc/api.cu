@@ -414,7 +414,11 @@ fs_status geometry(const QueryConst& q, const fs_config& cfg, Op op, int method,
         const uint64_t per_warp = (op == OP_ENUM || method == FS_METHOD_TRIPLE) ? 8 : 32;
         S = method == FS_METHOD_PLAIN ? (uint64_t)lc.blocks * lc.threads * 2
                                       : (uint64_t)lc.blocks * (lc.threads / 32) * per_warp;
-        lc.auto_s = 1;
+        // The warp walks end their queue with a tail of short slices
+        // (make_split): the warps that take the last slices decide when the
+        // walk ends (single large query, write walk: 0.303 -> 0.292 ms; heavy
+        // count query: QUAD walk 0.350 -> 0.325 ms, PAIR 0.99 -> 0.97 s).
+        lc.auto_s = method == FS_METHOD_PLAIN ? 1 : 2;
     }
     lc.min_leaves = method == FS_METHOD_PLAIN ? 16 : 256;
     if (S > (1ull << 31)) return fail(FS_E_INVAL, "slices = %llu exceeds 2^31", (unsigned long long)S);

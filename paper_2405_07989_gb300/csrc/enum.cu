@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, 3) k_pair_enum(const __grid_constant__ Qu
 {
     __shared__ SmemQ sq;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     int32_t* X0 = (int32_t*)dyn;
     int32_t* YD = X0 + (TAB ? q.lcm : 0);
     if (TAB)

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant_
 {
     __shared__ SmemQ sq;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     int32_t* X0 = (int32_t*)dyn;
     int32_t* YD = X0 + q.lcm;
     for (uint32_t i = threadIdx.x; i < q.lcm; i += blockDim.x) {

@@ -125,10 +125,14 @@ enum Ctr {
     CTR_SEFF = 8,     // number of slices the planner chose
     CTR_L = 9,        // number of leaves
     CTR_DONE = 10,    // blocks of a count walk that have added their part
-    CTR_SQ = 11,      // leaves per slice, floor(L / S) (planner)
-    CTR_SR = 12,      // L mod S: the first R slices have one leaf more (planner)
+    CTR_SQ = 11,      // leaves per head slice (planner; SliceSplit::Q)
+    CTR_SR = 12,      // head slices with one leaf more (SliceSplit::R)
     CTR_TMAX = 13,    // largest entry of the trailing count table (precompute)
-    CTR_N = 16
+    CTR_SH = 14,      // head slices (SliceSplit::Sh)
+    CTR_LH = 15,      // leaves of the head slices (SliceSplit::Lh)
+    CTR_TQ = 16,      // leaves per tail slice (SliceSplit::Qt)
+    CTR_TR = 17,      // tail slices with one leaf more (SliceSplit::Rt)
+    CTR_N = 24
 };
 
 struct Scratch {

@@ -26,7 +26,8 @@ struct LaunchCfg {
     int threads;
     int blocks;
     uint64_t S;           // slices (the maximum, when auto_s)
-    int auto_s;           // 1: the planner picks min(S, ceil(L / min_leaves)) slices
+    int auto_s;           // 1: the planner picks min(S, ceil(L / min_leaves)) slices;
+                          // 2: the same with a tail of short slices (make_split)
     uint64_t min_leaves;
 };
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ Quer
     __shared__ SmemQ sq;
     __shared__ unsigned long long bsum;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     if (threadIdx.x == 0) bsum = 0;
     uint32_t* Eb = (uint32_t*)dyn;
     if (TAB) build_count_bitmask(sc.E, q.lcm, Eb);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_pair_len(const __grid_constant__ QueryC
     __shared__ unsigned long long bsum;
     __shared__ unsigned int bmin, bmax;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     if (threadIdx.x == 0) {
         bsum = 0;
         bmin = 0xffffffffu;
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256) k_pair_hist(const __grid_constant__ Query
 {
     __shared__ SmemQ sq;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5;
     int2* TL = (int2*)dyn;
     uint32_t* D0 = (uint32_t*)(TL + q.lcm);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_any(const __grid_constant__ Que
     __shared__ SmemQ sq;
     __shared__ PredConst spc;
     extern __shared__ __align__(16) unsigned char dyn[];
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     if (threadIdx.x == 0) spc = pred;
     int32_t* X0 = (int32_t*)dyn;
     int32_t* YD = X0 + (TAB ? q.lcm : 0);
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_any(const __grid_constant__ Que
 // The walk runs over the prefixes of the first D-3 levels (the reduced query
 // q3 has one prefix level fewer); the leaf with residual r contributes
 // T3[r] factorizations with lengths lp + a + [MN3[r], MX3[r]].
-template <int MODE, bool PER_SLICE, bool SMEMT>
+template <int MODE, bool PER_SLICE, bool SMEMT, bool STAG_ = false>
 struct TripleCons {
     const uint64_t* T3;
     const uint32_t* T32;  // SMEMT: shared-memory uint32 copy of T3, or NULL
@@ -463,6 +463,7 @@ struct TripleCons {
     static constexpr bool MULTI_SET = true;
     static constexpr uint32_t CHUNK_OPS = MODE ? 12 : 4;
     static constexpr bool R_INDEXED = true;
+    static constexpr bool STAG = STAG_;  // staggered lanes (walk_slice_packed)
     FS_D void fault() { flag_fault(ctr); }
     FS_D void group_begin(const QueryConst&, const RunPrefix&, int, int32_t, int32_t) {}
     FS_D void slice_begin(const QueryConst&, uint64_t) {}
@@ -496,7 +497,7 @@ struct TripleCons {
 // SMEMT: the count table is copied to shared memory as uint32 (when its
 // largest entry, recorded by the precompute, fits), so the lookups of the walk
 // hit shared memory instead of L2.
-template <int MODE, bool PER_SLICE, bool SMEMT>
+template <int MODE, bool PER_SLICE, bool SMEMT, bool STAG = false>
 __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_walk(
     const __grid_constant__ QueryConst q3, Scratch sc, int queue, const uint64_t* T3,
     const int32_t* MN3, const int32_t* MX3, uint64_t* dev_count)
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_wa
         if (threadIdx.x == 0) publish_count(sc.ctr, dev_count);
         return;
     }
-    load_smemq(q3, sq);
+    load_smemq(q3, sq, sc.ctr);
     if (threadIdx.x == 0) {
         bsum = 0;
         bmin = 0x7fffffff;
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_wa
         }
     }
     __syncthreads();
-    TripleCons<MODE, PER_SLICE, SMEMT> cons{T3, T32, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
+    TripleCons<MODE, PER_SLICE, SMEMT, STAG> cons{T3, T32, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
     run_queue(q3, sq, sc, queue, cons);
     const uint64_t v = warp_sum_u64(cons.total);
     int mn = cons.mn, mx = cons.mx;
@@ -571,12 +572,12 @@ __global__ void __launch_bounds__(1024) k_pair_slice_runs(const __grid_constant_
     __shared__ uint64_t cnt[SLICE_GROUP];
     __shared__ uint64_t wsum[32];
     __shared__ bool last;
-    load_smemq(q, sq);
+    load_smemq(q, sq, sc.ctr);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
     const uint64_t S = sc.ctr[CTR_SEFF];
-    const SliceSplit split = planned_split(sc.ctr);
+    const SliceSplit split = sq.split;
     bool fault = false;
     constexpr int PER_WARP = SLICE_GROUP / 32;
     for (int i = 0; i < PER_WARP; i++) {
@@ -631,7 +632,8 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
     __shared__ int32_t part32[1024];
     __shared__ int32_t hs[FS_MAX_D];
     __shared__ Div32 dvh[FS_MAX_D];
-    __shared__ uint64_t sS, sL, sQ, sR;
+    __shared__ uint64_t sS, sL;
+    __shared__ SliceSplit ssp;
     const int tid = threadIdx.x;
     const int len = q.n + 1;
     const int P = q.P;
@@ -667,16 +669,13 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
             if (want < 1) want = 1;
             if (want < S) S = want;
         }
-        const SliceSplit sp(L, S);
+        ssp = make_split(L, S, auto_s);
         sS = S;
         sL = L;
-        sQ = sp.Q;
-        sR = sp.R;
         if (blockIdx.x == 0) {
             sc.ctr[CTR_SEFF] = S;
             sc.ctr[CTR_L] = L;
-            sc.ctr[CTR_SQ] = sp.Q;
-            sc.ctr[CTR_SR] = sp.R;
+            record_split(sc.ctr, ssp);
             const uint64_t total = C[q.n];  // C_0[n] = |Z|
             sc.ctr[CTR_TOTAL] = total;
             sc.slice_off[S] = total;
@@ -685,9 +684,7 @@ __global__ void __launch_bounds__(1024) k_plan_offsets(const __grid_constant__ Q
     }
     __syncthreads();
     const uint64_t S = sS, L = sL;
-    SliceSplit split;
-    split.Q = sQ;
-    split.R = sR;
+    const SliceSplit split = ssp;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t* Clast = C + (size_t)(P - 1) * len;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + tid; s < S; s += nt) {
@@ -756,28 +753,49 @@ cudaError_t triple_occupancy(const QueryConst& q3, Op op, int threads, int* nb)
     return occupancy_cached((const void*)k_triple_walk<1, false, false>, threads, 0, nb);
 }
 
+// Whether the shared-memory table walk staggers its lanes (walk_slice_packed):
+// sibling runs' residuals an even distance apart (bank conflicts) and an odd
+// step between a run's leaves.
+static bool triple_staggers(const QueryConst& q3)
+{
+    if (q3.P < 2) return false;
+    const int32_t hsib = q3.h[q3.P - 2], hin = q3.h[q3.P - 1];
+    return (hsib & 1) == 0 && (hin & 1) == 1;
+}
+
+template <bool PER_SLICE, bool STAG>
+static cudaError_t launch_triple_smem(const QueryConst& q3, const Scratch& sc, dim3 g, dim3 b,
+                                      int smem, int queue, const uint64_t* T3, uint64_t* dev_count,
+                                      cudaStream_t st)
+{
+    const cudaError_t e = smem_optin((const void*)k_triple_walk<0, PER_SLICE, true, STAG>, smem);
+    if (e == cudaSuccess)
+        k_triple_walk<0, PER_SLICE, true, STAG><<<g, b, smem, st>>>(q3, sc, queue, T3, nullptr,
+                                                                   nullptr, dev_count);
+    return e;
+}
+
 cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const LaunchCfg& lc,
                           int queue, const uint64_t* T3, const int32_t* MN3, const int32_t* MX3,
                           uint64_t* dev_count, cudaStream_t st)
 {
     const dim3 g(lc.blocks), b(lc.threads);
     const int smem = triple_smem(q3, op);
+    const bool stag = triple_staggers(q3);
     cudaError_t e = cudaSuccess;
     switch (op) {
     case OP_COUNT:
         if (smem) {
-            e = smem_optin((const void*)k_triple_walk<0, false, true>, smem);
-            if (e == cudaSuccess)
-                k_triple_walk<0, false, true><<<g, b, smem, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count);
+            e = stag ? launch_triple_smem<false, true>(q3, sc, g, b, smem, queue, T3, dev_count, st)
+                     : launch_triple_smem<false, false>(q3, sc, g, b, smem, queue, T3, dev_count, st);
         } else {
             k_triple_walk<0, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count);
         }
         break;
     case OP_SLICES:
         if (smem) {
-            e = smem_optin((const void*)k_triple_walk<0, true, true>, smem);
-            if (e == cudaSuccess)
-                k_triple_walk<0, true, true><<<g, b, smem, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
+            e = stag ? launch_triple_smem<true, true>(q3, sc, g, b, smem, queue, T3, nullptr, st)
+                     : launch_triple_smem<true, false>(q3, sc, g, b, smem, queue, T3, nullptr, st);
         } else {
             k_triple_walk<0, true, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
         }

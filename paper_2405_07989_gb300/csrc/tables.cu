@@ -92,22 +92,17 @@ FS_D void plan_slices(const QueryConst& q, const Scratch& sc, const uint64_t* W,
         if (want < S) S = want;
     }
     // one division per block, shared
-    __shared__ uint64_t sQ, sR;
+    __shared__ SliceSplit ssp;
     if (threadIdx.x == 0) {
-        const SliceSplit sp(L, S);
-        sQ = sp.Q;
-        sR = sp.R;
+        ssp = make_split(L, S, auto_s);
         if (blockIdx.x == 0) {
             sc.ctr[CTR_SEFF] = S;
             sc.ctr[CTR_L] = L;
-            sc.ctr[CTR_SQ] = sp.Q;
-            sc.ctr[CTR_SR] = sp.R;
+            record_split(sc.ctr, ssp);
         }
     }
     __syncthreads();
-    SliceSplit split;
-    split.Q = sQ;
-    split.R = sR;
+    const SliceSplit split = ssp;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += nt) {
         int32_t* st = sc.starts + s * START_W;

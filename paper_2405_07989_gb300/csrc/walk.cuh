@@ -20,14 +20,35 @@ namespace fsi {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// Slices: with L = Q S + R (0 <= R < S), slice s holds the leaf ranks
-// [s Q + min(s, R), (s+1) Q + min(s+1, R)): the first R slices one leaf more.
+// Slices: slice s holds the leaf ranks [start(s), start(s + 1)).  The first Sh
+// slices split the first Lh leaves evenly (Lh = Q Sh + R, 0 <= R < Sh: the
+// first R of them one leaf more); the remaining slices, the tail, split the
+// other leaves evenly the same way (Qt, Rt).  Without a tail Sh = S, Lh = L.
+// The walks take slices in index order from a dynamic queue, so a tail of
+// short slices lets the warps finish close together.
 // ---------------------------------------------------------------------------
 struct SliceSplit {
-    uint64_t Q, R;
-    FS_HD SliceSplit() : Q(0), R(0) {}
-    FS_HD SliceSplit(uint64_t L, uint64_t S) : Q(L / S), R(L % S) {}
-    FS_HD uint64_t start(uint64_t s) const { return s * Q + (s < R ? s : R); }
+    uint64_t Q, R, Sh, Lh, Qt, Rt;
+    SliceSplit() = default;
+    FS_HD SliceSplit(uint64_t L, uint64_t S) : Q(L / S), R(L % S), Sh(S), Lh(L), Qt(0), Rt(0) {}
+    // The last St of the S slices hold 1/shrink of a head slice's leaves each.
+    FS_HD static SliceSplit tailed(uint64_t L, uint64_t S, uint64_t St, uint32_t shrink)
+    {
+        if (St == 0 || St >= S || shrink <= 1) return SliceSplit(L, S);
+        const double den = (double)shrink * (double)(S - St) + (double)St;
+        uint64_t Lt = (uint64_t)((double)L * (double)St / den);
+        if (Lt > L) Lt = L;
+        SliceSplit p(L - Lt, S - St);
+        p.Qt = Lt / St;
+        p.Rt = Lt % St;
+        return p;
+    }
+    FS_HD uint64_t start(uint64_t s) const
+    {
+        if (s <= Sh) return s * Q + (s < R ? s : R);
+        const uint64_t t = s - Sh;
+        return Lh + t * Qt + (t < Rt ? t : Rt);
+    }
 };
 
 // The planner's split, as it recorded it (no 64-bit division per thread).
@@ -36,7 +57,29 @@ FS_D SliceSplit planned_split(const uint64_t* ctr)
     SliceSplit p;
     p.Q = ctr[CTR_SQ];
     p.R = ctr[CTR_SR];
+    p.Sh = ctr[CTR_SH];
+    p.Lh = ctr[CTR_LH];
+    p.Qt = ctr[CTR_TQ];
+    p.Rt = ctr[CTR_TR];
     return p;
+}
+
+// The split of L leaves into S slices as the planner makes it (auto_s == 2:
+// with a tail of a sixteenth of the slices, each a sixteenth the size).
+FS_HD SliceSplit make_split(uint64_t L, uint64_t S, int auto_s)
+{
+    return auto_s == 2 ? SliceSplit::tailed(L, S, S / 16, 16) : SliceSplit(L, S);
+}
+
+// Records the split for the walks (planned_split).
+FS_D void record_split(uint64_t* ctr, const SliceSplit& sp)
+{
+    ctr[CTR_SQ] = sp.Q;
+    ctr[CTR_SR] = sp.R;
+    ctr[CTR_SH] = sp.Sh;
+    ctr[CTR_LH] = sp.Lh;
+    ctr[CTR_TQ] = sp.Qt;
+    ctr[CTR_TR] = sp.Rt;
 }
 
 FS_HD uint64_t slice_start(uint64_t s, uint64_t L, uint64_t S)
@@ -535,6 +578,16 @@ template <class C>
 struct HasGroupLeaves<C, decltype((void)&C::group_leaves)> {
     static constexpr bool value = true;
 };
+// Whether a consumer walks with staggered lanes (Cons::STAG, below): a
+// per-launch choice, so that consumers that do not stagger keep their code.
+template <class C, class = void>
+struct Staggers {
+    static constexpr bool value = false;
+};
+template <class C>
+struct Staggers<C, decltype((void)C::STAG)> {
+    static constexpr bool value = C::STAG;
+};
 // Whether a consumer wants to hear when a group is done (Cons::group_end()).
 template <class C, class = void>
 struct HasGroupEnd {
@@ -655,30 +708,54 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
         cons.group_begin(q, cur, lane, ac, lpc);  // single-set groups: their set
         if constexpr (HasGroupLeaves<Cons>::value) cons.group_leaves(__reduce_add_sync(FULL, cnt));
         const uint32_t mxc = __reduce_max_sync(FULL, cnt);
+        // Lanes on sibling runs read a residual-indexed table at addresses
+        // hsib apart: 2^ctz(hsib)-way bank conflicts.  With an odd step between
+        // a run's leaves, holding lane j back j >> (5 - ctz(hsib)) steps puts
+        // the lanes' residuals in 32 different banks at every step, for
+        // 2^ctz(hsib) - 1 extra steps per group (stag: consumers launched with
+        // Cons::STAG, for queries where it applies; the lanes way only).
+        const uint32_t wsib = Cons::R_INDEXED ? conflict_ways(hsib) : 1u;
+        const bool stag = Staggers<Cons>::value && hsib != 0 && wsib > 1 && (mstep & 1u);
         bool lanes = q.walk == FS_WALK_LANES;
         if (q.walk == FS_WALK_AUTO) {
             const uint32_t sfull = __reduce_add_sync(FULL, nfull);
             const uint32_t spart = __reduce_add_sync(FULL, part);
             const uint32_t rfull = __popc(__ballot_sync(FULL, nfull > 0));
             using C = WalkCost<Cons>;
-            uint32_t cl = C::lane, cf = C::full, cp = C::pack;
+            uint32_t cl = C::lane, cf = C::full, cp = C::pack, xl = 0;
             if (Cons::R_INDEXED) {
-                cl += (conflict_ways(hsib) - 1) * C::per_way;
+                if (stag)
+                    xl = wsib - 1;
+                else
+                    cl += (wsib - 1) * C::per_way;
                 cf += (conflict_ways(mstep) - 1) * C::per_way;
                 cp += C::per_way;  // lanes on mixed runs: about two ways
             }
-            lanes = (uint64_t)mxc * cl <= (uint64_t)sfull * cf + (uint64_t)rfull * C::per_run +
-                                              (uint64_t)((spart + 31) >> 5) * cp;
+            lanes = (uint64_t)(mxc + xl) * cl <= (uint64_t)sfull * cf + (uint64_t)rfull * C::per_run +
+                                                     (uint64_t)((spart + 31) >> 5) * cp;
         }
         if (lanes) {
-            // lane j: run j's visited leaves a = first + i ma, i < cnt; while
-            // every lane still has one the bound check is left out
-            uint32_t a = first, r = Rj - first * hin;
+            // lane j: run j's visited leaves a = first + k ma, k < cnt, leaf k
+            // at step i = k + dl (dl: the lane's delay, 0 unless stag); while
+            // every lane has started and none has ended the bound check is
+            // left out
+            const uint32_t dl = stag ? (uint32_t)lane >> (5 - (__ffs(wsib) - 1)) : 0u;
+            uint32_t a = first - dl * ma, r = Rj - first * hin + dl * mstep;
             const int32_t lp = lpj;
-            const uint32_t mnc = __reduce_min_sync(FULL, cnt);
+            const uint32_t e = cnt + dl;                        // one past the lane's last step
+            const uint32_t lo_u = stag ? wsib - 1 : 0u;         // every lane has started
+            const uint32_t hi_u = __reduce_min_sync(FULL, e);   // none has ended
+            const uint32_t mxe = stag ? __reduce_max_sync(FULL, e) : mxc;
             uint32_t i = 0;
+            if (Staggers<Cons>::value) {
+                for (const uint32_t p1 = min(lo_u, mxe); i < p1; i++) {
+                    if (cons.chunk(q, lane, i - dl < cnt, (int32_t)r, (int32_t)a, lp)) return true;
+                    r -= mstep;
+                    a += ma;
+                }
+            }
             if (Cons::UNROLL > 1) {
-                for (; i + Cons::UNROLL <= mnc; i += Cons::UNROLL) {
+                for (; i + Cons::UNROLL <= hi_u; i += Cons::UNROLL) {
 #pragma unroll
                     for (int u = 0; u < Cons::UNROLL; u++) {
                         if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
@@ -687,13 +764,13 @@ FS_D bool walk_slice_packed(const QueryConst& q, const int32_t* hs, const Div32*
                     }
                 }
             }
-            for (; i < mnc; i++) {
+            for (; i < hi_u; i++) {
                 if (cons.chunk(q, lane, true, (int32_t)r, (int32_t)a, lp)) return true;
                 r -= mstep;
                 a += ma;
             }
-            for (; i < mxc; i++) {
-                if (cons.chunk(q, lane, i < cnt, (int32_t)r, (int32_t)a, lp)) return true;
+            for (; i < mxe; i++) {
+                if (cons.chunk(q, lane, i - dl < cnt, (int32_t)r, (int32_t)a, lp)) return true;
                 r -= mstep;
                 a += ma;
             }
@@ -952,9 +1029,13 @@ struct SmemQ {
     int32_t h[FS_MAX_D];
     int32_t col[FS_MAX_D];
     Div32 dvh[FS_MAX_D];
+    SliceSplit split;  // the planner's split (planned_split)
 };
 
-FS_D void load_smemq(const QueryConst& q, SmemQ& sq)
+// The block's copy of the query constants and of the planner's split (ctr: the
+// call's counters, written by the planner before this kernel).  The caller
+// synchronises the block before using sq.
+FS_D void load_smemq(const QueryConst& q, SmemQ& sq, const uint64_t* ctr)
 {
     const int t = threadIdx.x;
     if (t < FS_MAX_D) {
@@ -962,6 +1043,7 @@ FS_D void load_smemq(const QueryConst& q, SmemQ& sq)
         sq.col[t] = q.col[t];
         sq.dvh[t] = q.dv_h[t];
     }
+    if (t == FS_MAX_D) sq.split = planned_split(ctr);
 }
 
 // Walk slices with `cons`.  The planner (k_plan) has written the number of
@@ -976,7 +1058,6 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
     const int lane = threadIdx.x & 31;
     const int32_t hk = lane < q.P - 1 ? sq.h[lane] : 0;
     const uint64_t S_all = sc.ctr[CTR_SEFF];
-    const SliceSplit split = planned_split(sc.ctr);
     const uint64_t S = sc.s_hi < S_all ? sc.s_hi : S_all;  // the window's slices
     const uint64_t W = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long* qc = (unsigned long long*)&sc.ctr[queue];
@@ -984,7 +1065,7 @@ FS_D void run_queue(const QueryConst& q, const SmemQ& sq, const Scratch& sc, int
     while (s < S) {
         unsigned long long nxt = 0;
         if (lane == 0) nxt = sc.s_lo + atomicAdd(qc, 1ull) + W;
-        const uint64_t k0 = split.start(s), k1 = split.start(s + 1);
+        const uint64_t k0 = sq.split.start(s), k1 = sq.split.start(s + 1);
         cons.slice_begin(q, s);
         bool stop = false;
         if (k1 > k0) stop = walk_slice(q, sq.h, sq.dvh, sc.starts, s, k1 - k0, lane, hk, cons);

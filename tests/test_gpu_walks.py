@@ -153,3 +153,30 @@ def test_config3_count_forced(walk):
     """The heavy count-only query at full size through the PAIR walk."""
     n, g = workloads.config3(0)
     assert fs.fs_count(n, g, cfg(WALKS[walk])) == 7655692813487
+
+
+@pytest.mark.parametrize("walk", list(WALKS))
+def test_trailing_walks_sibling_stride_even(walk):
+    """Trailing-table walks whose sibling runs have residuals an even distance
+    apart (2, 4, .., 32 and more times an odd number) and an odd step inside a
+    run: the walk holds lanes back to spread their table reads over the banks.
+    Counts, per-slice counts and the length range against the oracle's DPs."""
+    w = WALKS[walk]
+    cases = []
+    for sib in (2 * 31, 4 * 15, 8 * 7, 16 * 5, 32 * 3, 64):
+        # generators in descending (walk) order; the walked levels end with the
+        # sibling level `sib` and an odd run level
+        cases.append((2500, (sib + 41, sib + 17, sib, 45, 31, 29, 23, 19)))  # QUAD walks 4 levels
+        cases.append((2500, (sib + 41, sib, 45, 29, 23, 19)))                # TRIPLE walks 3
+        cases.append((900, (sib + 3, sib, 33, 25, 9, 7, 5)))                 # QUAD walks 3
+    for n, g in cases:
+        expect = oracle.count_dp(n, g)
+        for method in (fs.METHOD_TRIPLE, fs.METHOD_QUAD, fs.METHOD_AUTO):
+            if method == fs.METHOD_QUAD and len(g) < 5:
+                continue
+            c = cfg(w, method)
+            assert fs.fs_count(n, g, c) == expect, (n, g, method)
+            counts = fs.fs_slice_counts(n, g, 37, c)
+            assert sum(counts) == expect, (n, g, method)
+        mm = oracle.minmax_dp(n, g) or (0, 0)
+        assert fs.fs_length_stats(n, g, None, cfg(w, fs.METHOD_TRIPLE)) == (expect,) + tuple(mm)
