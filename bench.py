@@ -874,12 +874,18 @@ def serving_extras(fs, workloads, rate: float, nreq: int, hist: bool = True):
                      (fs.REQ_ENUMERATE, "enumerate")):
         by_op[name] = pct([r["t_done"] - r["t_submit"] for r in rs if r["op"] == op])
     ran = [r for r in rs if r["t_start"] > 0]
-    jobs = [r for r in ran if r["t_job"] > 0]
+    # direct: a count / length request run as a job from the start (no batch)
+    direct = [r for r in ran if r["t_job"] > 0 and r["t_start"] == r["t_job"]]
+    direct_t = {r["ticket"] for r in direct}
+    batched = [r for r in ran if r["ticket"] not in direct_t]
+    jobs = [r for r in batched if r["t_job"] > 0]
     stages = {"queue": pct([r["t_start"] - r["t_submit"] for r in ran]),
-              "batch": pct([r["t_counted"] - r["t_start"] for r in ran]),
+              "batch": pct([r["t_counted"] - r["t_start"] for r in batched]),
+              "direct_job": pct([r["t_counted"] - r["t_start"] for r in direct]),
               "job_wait": pct([r["t_job"] - r["t_counted"] for r in jobs]),
               "job": pct([r["t_done"] - r["t_job"] for r in jobs]),
-              "answer": pct([r["t_done"] - r["t_counted"] for r in ran if r["t_job"] == 0])}
+              "answer": pct([r["t_done"] - r["t_counted"] for r in ran
+                             if r["t_job"] == 0 or r["ticket"] in direct_t])}
     status = {}
     for r in rs:
         status[fs.status_name(r["status"])] = status.get(fs.status_name(r["status"]), 0) + 1

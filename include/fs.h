@@ -375,7 +375,14 @@ fs_status fs_reserve(uint64_t bytes, void* stream);
  * count and length range.  Two kinds of request then need device work of
  * their own (a "job"): an ENUMERATE (its rows, count * d * elem_bytes bytes)
  * and a LENGTHS request with hist = 1 (its histogram, (floor(n / min g) + 1)
- * * 8 bytes).  A job's bytes, exact, are admitted against the device memory
+ * * 8 bytes).  A COUNT or LENGTHS request whose walk would be long skips the
+ * batch and runs as a job from the start (fs_count_async or
+ * fs_length_stats_async on a job stream, its results read back from there):
+ * one long walk would otherwise hold up the whole batch's answers.  "Long" is
+ * an estimate of the leaves the batched walk visits, the lattice volume
+ * prod_i (n + S) / ((i + 1) g_i) over the generators it walks (descending, all
+ * but the last four for d >= 5, three for d = 4, two otherwise; S their sum),
+ * against direct_leaves.  A job's bytes, exact, are admitted against the device memory
  * budget: larger than the whole budget -> FS_E_CAPACITY (count and range still
  * reported; so is a histogram whose PAIR walk would visit more than
  * hist_max_leaves leaves, |Z(n; g_1..g_{d-2}, gcd(g_{d-1}, g_d))| in descending
@@ -398,6 +405,9 @@ typedef struct fs_server_config {
     int32_t job_streams;        /* jobs in flight (enumerates, histograms); 0 = 4 */
     uint64_t hist_max_leaves;   /* a histogram job whose walk visits more leaves is refused
                                    with FS_E_CAPACITY; 0 = 2^34 */
+    uint64_t direct_leaves;     /* a COUNT or LENGTHS request whose walk is estimated to
+                                   visit more leaves runs as a job of its own instead of in
+                                   a batch; 0 = 2^24 */
 } fs_server_config;
 
 typedef struct fs_request {
@@ -422,8 +432,10 @@ typedef struct fs_response {
                            fs_enumerate_ex with the request's keep_order); LENGTHS with
                            hist: floor(n / min g) + 1 uint64 bins (as fs_length_stats) */
     double t_submit;    /* seconds since fs_server_create */
-    double t_start;     /* when its batch was launched (the end of its queue wait) */
-    double t_counted;   /* when its batch's results were collected */
+    double t_start;     /* when its batch was launched (the end of its queue wait);
+                           a request run as a job from the start: its job's launch */
+    double t_counted;   /* when its batch's results were collected (run as a job
+                           from the start: when the job's results were) */
     double t_job;       /* when its job was launched (0: no job) */
     double t_done;      /* when its result was seen complete */
 } fs_response;

@@ -66,7 +66,7 @@ class fs_server_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
                 ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
                 ("window_us", ctypes.c_int32), ("job_streams", ctypes.c_int32),
-                ("hist_max_leaves", ctypes.c_uint64)]
+                ("hist_max_leaves", ctypes.c_uint64), ("direct_leaves", ctypes.c_uint64)]
 
 
 class fs_request(ctypes.Structure):
@@ -549,9 +549,10 @@ class Server:
 
     def __init__(self, mem_budget_bytes: int = 0, table_bytes: int = 0, max_batch: int = 0,
                  slots: int = 0, window_us: int = 0, job_streams: int = 0,
-                 hist_max_leaves: int = 0):
+                 hist_max_leaves: int = 0, direct_leaves: int = 0):
         cfg = fs_server_config(int(mem_budget_bytes), int(table_bytes), int(max_batch),
-                               int(slots), int(window_us), int(job_streams), int(hist_max_leaves))
+                               int(slots), int(window_us), int(job_streams), int(hist_max_leaves),
+                               int(direct_leaves))
         h = ctypes.c_void_p(0)
         _check(lib().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

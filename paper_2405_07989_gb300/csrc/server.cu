@@ -1,5 +1,5 @@
 // Serving: a request loop with continuous batching, built on the batch-slot,
-// enumerate and length entry points of the C ABI.
+// count, enumerate and length entry points of the C ABI.
 //
 // Requests (count, length range with an optional histogram, enumerate) are
 // queued by fs_server_submit.  One worker thread admits them into reusable
@@ -11,8 +11,11 @@
 // histogram then becomes a job, admitted in arrival order when its exact
 // output bytes fit the server's device memory budget (refused with
 // FS_E_CAPACITY when they exceed the whole budget) and one of the job streams
-// is idle, so several jobs run at once beside the batches.  Completed requests
-// are collected by fs_server_poll with a timestamp per stage.
+// is idle, so several jobs run at once beside the batches.  A count or length
+// request whose walk is long skips the batch and is a job from the start
+// (direct): the single-query walk takes it with the whole GPU, and the
+// batch's other answers do not wait for it.  Completed requests are collected
+// by fs_server_poll with a timestamp per stage.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,6 +40,7 @@ struct Req {
     double t_start;    // its batch was launched
     double t_counted;  // its batch's results were collected
     double t_job;      // its job was launched (0: none)
+    bool direct;       // COUNT / LENGTHS run as a job of its own (no batch)
 };
 
 struct Slot {
@@ -54,12 +58,16 @@ struct Job {
     uint64_t count;
     uint32_t min_len, max_len;
     uint64_t off, bytes;  // output in the pool
+    bool refuse_hist;     // direct LENGTHS whose histogram is over the work bound
+    // whether the job holds pool memory: all but the direct ones without a histogram
+    bool pooled() const { return !req.direct || bytes > 0; }
 };
 
 struct JobLane {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     uint64_t* dscratch = nullptr;  // device counters the job writes (count, min, max)
+    uint64_t* hres = nullptr;      // pinned copy of them, for direct jobs
     bool busy = false;
     Job job;
 };
@@ -204,6 +212,27 @@ static double hist_walk_leaves(const fs_request& r)
     return v;
 }
 
+// Leaves the batched walk of a request visits, estimated from above by the
+// lattice volume: the walk takes the generators in descending order, all but
+// the last four (d >= 5 and n < 2^22), three (d >= 4) or two, and the prefixes
+// with sum a_i g_i <= n number at most prod_i (n + S) / ((i + 1) g_i) (S the
+// sum of those generators).  0 for a request the batch rejects anyway.
+static double batch_walk_leaves(const fs_request& r)
+{
+    if (r.d < 1 || r.d > FS_MAX_D || r.n < 0) return 0.0;
+    std::vector<double> g(r.gens, r.gens + r.d);
+    for (double x : g)
+        if (x < 1.0) return 0.0;
+    std::sort(g.begin(), g.end(), std::greater<double>());
+    const int k = (r.d >= 5 && r.n < (1 << 22)) ? 4 : (r.d >= 4 && r.n < (1 << 27)) ? 3 : 2;
+    const int m = std::max(0, r.d - k);
+    double S = 0.0;
+    for (int i = 0; i < m; i++) S += g[i];
+    double v = 1.0;
+    for (int i = 0; i < m; i++) v *= ((double)r.n + S) / ((double)(i + 1) * g[i]);
+    return v;
+}
+
 bool fs_server::step()
 {
     bool progress = false;
@@ -231,6 +260,7 @@ bool fs_server::step()
                 j.off = 0;
                 j.bytes = enum_job ? R.count * (uint64_t)q.r.d * (uint64_t)q.r.elem_bytes
                                    : ((uint64_t)q.r.n / min_gen(q.r) + 1) * 8;
+                j.refuse_hist = false;
                 job_wait.push_back(j);
             } else {
                 finish(q, st, R.count, R.min_len, R.max_len, nullptr);
@@ -240,14 +270,28 @@ bool fs_server::step()
         sl.busy = false;
         progress = true;
     }
-    // 2. finished jobs: their outputs stay reserved until released
+    // 2. finished jobs: their outputs stay reserved until released; a direct
+    // job's count (and length range) comes from its own walk
     for (JobLane& l : lanes) {
         if (!l.busy || cudaEventQuery(l.ev) != cudaSuccess) continue;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            held[l.job.req.ticket] = {l.job.off, l.job.bytes};
+        Job& j = l.job;
+        if (j.req.direct) {
+            j.req.t_counted = now();
+            j.count = l.hres[0];
+            if (j.req.r.op == FS_REQ_LENGTHS) {
+                j.min_len = (uint32_t)l.hres[1];
+                j.max_len = (uint32_t)l.hres[2];
+            }
         }
-        finish(l.job.req, FS_OK, l.job.count, l.job.min_len, l.job.max_len, pool.base + l.job.off);
+        if (!j.pooled()) {
+            finish(j.req, j.refuse_hist ? FS_E_CAPACITY : FS_OK, j.count, j.min_len, j.max_len, nullptr);
+        } else {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                held[j.req.ticket] = {j.off, j.bytes};
+            }
+            finish(j.req, FS_OK, j.count, j.min_len, j.max_len, pool.base + j.off);
+        }
         l.busy = false;
         progress = true;
     }
@@ -263,26 +307,33 @@ bool fs_server::step()
                 progress = true;
                 continue;
             }
-            bool ok;
-            {
+            bool ok = true;
+            if (j.pooled()) {
                 std::lock_guard<std::mutex> lk(mu);
                 ok = pool.alloc(j.bytes, &j.off);
             }
             if (!ok) break;  // wait for outputs to be released
             j.req.t_job = now();
+            if (j.req.direct) j.req.t_start = j.req.t_job;
             fs_config ec;
             fs_config_default(&ec);
             fs_status s;
+            uint64_t* hist = j.pooled() ? (uint64_t*)(pool.base + j.off) : nullptr;
             if (j.req.r.op == FS_REQ_ENUMERATE) {
                 ec.keep_order = j.req.r.keep_order;
                 s = fs_enumerate_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec, pool.base + j.off,
                                        j.count, j.req.r.elem_bytes, l.dscratch, l.st);
+            } else if (j.req.r.op == FS_REQ_COUNT) {
+                s = fs_count_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec, l.dscratch, l.st);
             } else {
-                s = fs_length_stats_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec,
-                                          (uint64_t*)(pool.base + j.off), l.dscratch, l.st);
+                s = fs_length_stats_async(j.req.r.n, j.req.r.gens, j.req.r.d, &ec, hist, l.dscratch,
+                                          l.st);
             }
+            if (s == FS_OK && j.req.direct &&
+                cudaMemcpyAsync(l.hres, l.dscratch, 3 * 8, cudaMemcpyDeviceToHost, l.st) != cudaSuccess)
+                s = FS_E_CUDA;
             if (s != FS_OK) {
-                {
+                if (j.pooled()) {
                     std::lock_guard<std::mutex> lk(mu);
                     pool.release(j.off, j.bytes);
                 }
@@ -298,6 +349,39 @@ bool fs_server::step()
             started = progress = true;
         }
         if (job_wait.empty()) break;
+    }
+    // 3b. long count / length requests become jobs of their own, in arrival
+    // order behind the jobs already waiting
+    {
+        std::vector<Req> direct;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto it = pending.begin(); it != pending.end();) {
+                if (it->direct) {
+                    direct.push_back(*it);
+                    it = pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (const Req& q : direct) {
+            Job j;
+            j.req = q;
+            j.count = 0;
+            j.min_len = j.max_len = 0;
+            j.off = 0;
+            j.bytes = 0;
+            j.refuse_hist = false;
+            if (q.r.op == FS_REQ_LENGTHS && q.r.hist) {
+                if (hist_walk_leaves(q.r) > (double)cfg.hist_max_leaves)
+                    j.refuse_hist = true;  // count and range only, then FS_E_CAPACITY
+                else
+                    j.bytes = ((uint64_t)q.r.n / min_gen(q.r) + 1) * 8;
+            }
+            job_wait.push_back(j);
+            progress = true;
+        }
     }
     // 4. admit arrived requests into a free slot.  A batch holds one class of
     // requests, that of the oldest one waiting: counts alone (count mode, no
@@ -399,6 +483,7 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
     if (s->cfg.window_us <= 0) s->cfg.window_us = 200;
     if (s->cfg.job_streams <= 0) s->cfg.job_streams = 4;
     if (s->cfg.hist_max_leaves == 0) s->cfg.hist_max_leaves = 1ull << 34;
+    if (s->cfg.direct_leaves == 0) s->cfg.direct_leaves = 1ull << 24;
     if (s->cfg.table_bytes == 0) s->cfg.table_bytes = 256ull << 20;
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&s->dev);
@@ -416,7 +501,8 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out)
         st = FS_E_NOMEM;
     for (int i = 0; st == FS_OK && i < s->cfg.job_streams; i++) {
         JobLane l;
-        if (fsi::dev_alloc((void**)&l.dscratch, 3 * 8) != cudaSuccess)
+        if (fsi::dev_alloc((void**)&l.dscratch, 3 * 8) != cudaSuccess ||
+            fsi::host_alloc((void**)&l.hres, 3 * 8) != cudaSuccess)
             st = FS_E_NOMEM;
         else if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
                  cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming) != cudaSuccess)
@@ -450,6 +536,7 @@ fs_status fs_server_submit(fs_server* s, const fs_request* r, uint64_t* ticket)
     q.r = *r;
     q.t_submit = s->now();
     q.t_start = q.t_counted = q.t_job = 0;
+    q.direct = r->op != FS_REQ_ENUMERATE && batch_walk_leaves(*r) > (double)s->cfg.direct_leaves;
     s->pending.push_back(q);
     *ticket = q.ticket;
     s->cv_in.notify_one();
@@ -505,6 +592,7 @@ fs_status fs_server_destroy(fs_server* s)
     if (s->pool.base) cudaFree(s->pool.base);
     for (JobLane& l : s->lanes) {
         if (l.dscratch) cudaFree(l.dscratch);
+        if (l.hres) cudaFreeHost(l.hres);
         if (l.st) cudaStreamDestroy(l.st);
         if (l.ev) cudaEventDestroy(l.ev);
     }

@@ -82,9 +82,15 @@ def check(resp, op, n, g, elem_bytes=2, keep_order=False, hist=False):
     if op in (fs.REQ_LENGTHS, fs.REQ_ENUMERATE) and c > 0:
         assert (resp["min_len"], resp["max_len"]) == oracle.minmax_dp(n, g)
     job = op == fs.REQ_ENUMERATE or (op == fs.REQ_LENGTHS and hist)
+    # a count or length request run as a job from the start (no batch) is
+    # launched, counted and answered by its job
+    direct = resp["t_job"] > 0 and resp["t_start"] == resp["t_job"]
     # the stages in order; a job's launch between the count and the answer
     assert resp["t_submit"] <= resp["t_start"] <= resp["t_counted"] <= resp["t_done"], resp
-    if job:
+    if direct:
+        assert op != fs.REQ_ENUMERATE and resp["t_counted"] <= resp["t_done"], resp
+        assert (resp["rows"] != 0) == hist, resp
+    elif job:
         assert resp["t_counted"] <= resp["t_job"] <= resp["t_done"], resp
     else:
         assert resp["t_job"] == 0.0 and resp["rows"] == 0, resp
@@ -275,3 +281,50 @@ def test_server_histogram_work_bound():
         assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(*big)
         check(got[ts], fs.REQ_LENGTHS, *small, hist=True)
         srv.release(ts)
+
+
+def test_server_direct_jobs():
+    """Count and length requests over the direct-job bound skip the batch and
+    run as single-query calls on the job streams (here the bound is one leaf,
+    so every such request with more than one leaf does), mixed with batched
+    enumerations: every response equals the oracle and the call alone; a
+    histogram over the work bound is still refused with its exact count and
+    range."""
+    reqs = workloads.config5(seed=7, nreq=120, n_max=2500)
+    with fs.Server(mem_budget_bytes=512 << 20, max_batch=32, job_streams=3,
+                   direct_leaves=1) as srv:
+        tickets = {}
+        for i, (_, op, n, g) in enumerate(reqs):
+            hist = op == fs.REQ_LENGTHS and i % 2 == 0
+            tickets[srv.submit(op, n, g, elem_bytes=2, hist=hist)] = (op, n, g, hist)
+        got = drain(srv, tickets)
+        direct = 0
+        for t, (op, n, g, hist) in tickets.items():
+            r = got[t]
+            check(r, op, n, g, hist=hist)
+            direct += r["t_job"] > 0 and r["t_start"] == r["t_job"]
+            if op == fs.REQ_ENUMERATE or hist:
+                srv.release(t)
+        assert direct >= sum(1 for op, _, _, _ in tickets.values() if op != fs.REQ_ENUMERATE) // 2
+    big = (2000, (11, 13, 17, 19, 23))
+    with fs.Server(mem_budget_bytes=64 << 20, hist_max_leaves=2000, direct_leaves=1) as srv:
+        tb = srv.submit(fs.REQ_LENGTHS, *big, hist=True)
+        r = drain(srv, [tb])[tb]
+        assert r["status"] == fs.FS_E_CAPACITY and r["rows"] == 0 and r["t_start"] == r["t_job"]
+        assert r["count"] == oracle.count_dp(*big)
+        assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(*big)
+
+
+def test_server_long_count_runs_direct():
+    """With the default bound, the heavy count query's generators at n = 20000
+    (a walk of about 10^7 leaves) run as a job of their own, next to short
+    counts that are batched."""
+    n, g = workloads.config3(0, n=20000)
+    with fs.Server(mem_budget_bytes=64 << 20) as srv:
+        tl = srv.submit(fs.REQ_COUNT, n, g)
+        ts = srv.submit(fs.REQ_COUNT, 500, (5, 7, 11, 13))
+        got = drain(srv, [tl, ts])
+        assert got[tl]["status"] == fs.FS_OK and got[tl]["count"] == oracle.count_dp(n, g)
+        assert got[tl]["t_start"] == got[tl]["t_job"] > 0
+        check(got[ts], fs.REQ_COUNT, 500, (5, 7, 11, 13))
+        assert got[ts]["t_job"] == 0.0
