@@ -542,6 +542,14 @@ fs_status fs_probe_int_rate(int kind, uint32_t iters, double* ops_per_s);
  * no GPU.  Returns the number of mismatches (0 = correct), -1 on bad input. */
 int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count);
 
+/* The planner's split of `leaves` leaf ranks into `slices` slices (Sec. 4), as
+ * the walks use it: starts (host, slices + 1 uint64) receives the first rank
+ * of every slice and `leaves` last.  tail = 0: equal slices (explicit slice
+ * counts); tail = 1: the split of a planner that picks its own slice count,
+ * whose last sixteenth of the slices hold a sixteenth of a regular slice each.
+ * Runs on the host, needs no GPU.  FS_E_INVAL for slices = 0 or a null starts. */
+fs_status fs_selftest_split(uint64_t leaves, uint64_t slices, int tail, uint64_t* starts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,8 @@ SIGNATURES = {
     "fs_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32,
                                          ctypes.POINTER(ctypes.c_double)]),
     "fs_selftest_division": (ctypes.c_int64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
+    "fs_selftest_split": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 
@@ -640,3 +642,10 @@ def fs_probe_int_rate(kind: int, iters: int = 4096) -> float:
 def fs_selftest_division(div: int, x0: int, count: int) -> int:
     """Host self test of the invariant-divisor division (no GPU needed)."""
     return int(lib().fs_selftest_division(int(div), int(x0), int(count)))
+
+
+def fs_selftest_split(leaves: int, slices: int, tail: bool) -> list:
+    """The planner's slice starts (host, no GPU): slices + 1 leaf ranks."""
+    out = (ctypes.c_uint64 * (int(slices) + 1))()
+    _check(lib().fs_selftest_split(int(leaves), int(slices), 1 if tail else 0, out))
+    return [int(x) for x in out]

@@ -1676,6 +1676,14 @@ fs_status fs_batch_autotune(const fs_query* queries, int nq, int mode, fs_config
     return s2;
 }
 
+fs_status fs_selftest_split(uint64_t leaves, uint64_t slices, int tail, uint64_t* starts)
+{
+    if (slices == 0 || !starts) return FS_E_INVAL;
+    const SliceSplit sp = make_split(leaves, slices, tail ? 2 : 1);
+    for (uint64_t s = 0; s <= slices; s++) starts[s] = sp.start(s);
+    return FS_OK;
+}
+
 int64_t fs_selftest_division(uint32_t div, uint32_t x0, uint32_t count)
 {
     if (div == 0 || div > 0x7fffffffu) return -1;

@@ -140,3 +140,31 @@ def test_invariant_division_exact(div):
 def test_invariant_division_exhaustive_small_divisors():
     for div in range(1, 300):
         assert fs.fs_selftest_division(div, 0, 20000) == 0
+
+
+@pytest.mark.parametrize("leaves,slices", [(0, 1), (1, 1), (5, 16), (1000, 16), (1000, 17),
+                                           (10**6, 38912), (3832670754382, 155648),
+                                           (16614104, 38912), (100, 1000), (2**62, 3)])
+def test_slice_split_covers_and_balances(leaves, slices):
+    """The planner's split: slice starts from 0 to the leaf count, never
+    decreasing.  Equal split: sizes differ by at most one.  With the tail (the
+    planner's own slice count): the first slices equal to within one, the last
+    sixteenth equal to within one and about a sixteenth of the others."""
+    for tail in (False, True):
+        st = fs.fs_selftest_split(leaves, slices, tail)
+        assert len(st) == slices + 1 and st[0] == 0 and st[-1] == leaves
+        sizes = [b - a for a, b in zip(st, st[1:])]
+        assert min(sizes) >= 0
+        nt = slices // 16 if tail else 0
+        head, tl = sizes[:slices - nt], sizes[slices - nt:]
+        assert max(head) - min(head) <= 1, (tail, leaves, slices)
+        if not tail or nt == 0:
+            assert max(sizes) - min(sizes) <= 1
+            assert st == [s * (leaves // slices) + min(s, leaves % slices) for s in range(slices + 1)]
+            continue
+        assert max(tl) - min(tl) <= 1
+        if min(head) >= 64:  # the tail slices are a sixteenth of a head slice (rounding aside)
+            ratio = (sum(tl) / len(tl)) / (sum(head) / len(head))
+            assert abs(ratio - 1 / 16) < 1e-3 + 2 / min(head), ratio
+    with pytest.raises(fs.FsError):
+        fs.fs_selftest_split(10, 0, True)
