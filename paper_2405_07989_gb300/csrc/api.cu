@@ -269,6 +269,8 @@ fs_status build_query(int64_t n, const uint32_t* gens, int d, const fs_config& c
     q.nw = q.P - 1;
     q.acc32 = q.lcm && 32.0 * ((double)n / q.h[q.P - 1] + 1.0) * ((double)n / q.lcm + 1.0) <
                            4294967295.0;
+    q.fdiv = q.lcm >= 2 && (uint64_t)n * q.lcm < (1ull << 32);
+    q.lcm_m1 = q.fdiv ? (uint32_t)(((1ull << 32) + q.lcm - 1) / q.lcm) : 0u;
     // common-divisor skipping for the pair walk (trailing gcd G) and for the
     // trailing-three / trailing-four walks (gcd of the last three / four)
     {

@@ -104,6 +104,13 @@ struct QueryConst {
     // takes at most 32 (n / h_in + 1) leaves of a group and each has at most
     // n / lcm + 1 completions (PAIR count walk; set by build_query).
     int32_t acc32;
+    // floor(x / lcm) = umulhi(x, lcm_m1) for every residual x <= n when fdiv:
+    // with lcm_m1 = ceil(2^32 / lcm) = (2^32 + e) / lcm, 0 <= e < lcm, the
+    // product x lcm_m1 / 2^32 exceeds x / lcm by x e / (lcm 2^32) < 1 / lcm
+    // while n lcm < 2^32, too little to reach the next integer (set by
+    // build_query for lcm >= 2).
+    uint32_t lcm_m1;
+    int32_t fdiv;
 };
 
 // ---------------------------------------------------------------------------

@@ -20,8 +20,9 @@ namespace fsi {
 // lookups at scattered w never meet in a bank (4 lcm bytes, 64 KB at most).
 // ACC32: a lane sums its counts of one sibling group in 32 bits and adds
 // them to its 64-bit total when the group is done (QueryConst::acc32 bounds
-// that sum).
-template <bool TAB, bool PER_SLICE, bool ACC32>
+// that sum).  FDIV: the quotient by lcm is one multiply-high
+// (QueryConst::fdiv).
+template <bool TAB, bool PER_SLICE, bool ACC32, bool FDIV = false>
 struct CountCons {
     const uint32_t* Eb;  // TAB: the replicated bitmask
     uint64_t* slice_cnt;
@@ -59,7 +60,7 @@ struct CountCons {
         if (valid) {
             uint32_t c;
             if (TAB) {
-                const uint32_t qq = div32((uint32_t)r, q.dv_lcm);
+                const uint32_t qq = FDIV ? __umulhi((uint32_t)r, q.lcm_m1) : div32((uint32_t)r, q.dv_lcm);
                 const uint32_t w = (uint32_t)r - qq * q.lcm;
                 const uint32_t m = Eb[(w & ~31u) | (uint32_t)lane];
                 c = qq + (__funnelshift_r(m, m, w) & 1u);
@@ -88,7 +89,7 @@ FS_D void build_count_bitmask(const int8_t* E, uint32_t lcm, uint32_t* Eb)
     }
 }
 
-template <bool TAB, bool PER_SLICE, bool ACC32>
+template <bool TAB, bool PER_SLICE, bool ACC32, bool FDIV = false>
 __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ QueryConst q,
                                                     Scratch sc, int queue, uint64_t* dev_count)
 {
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) k_pair_count(const __grid_constant__ Quer
     uint32_t* Eb = (uint32_t*)dyn;
     if (TAB) build_count_bitmask(sc.E, q.lcm, Eb);
     __syncthreads();
-    CountCons<TAB, PER_SLICE, ACC32> cons{Eb, sc.slice_cnt, 0, 0, 0u, sc.ctr};
+    CountCons<TAB, PER_SLICE, ACC32, FDIV> cons{Eb, sc.slice_cnt, 0, 0, 0u, sc.ctr};
     run_queue(q, sq, sc, queue, cons);
     uint64_t v = warp_sum_u64(cons.total);
     if ((threadIdx.x & 31) == 0) atomicAdd(&bsum, (unsigned long long)v);
@@ -236,7 +237,9 @@ __global__ void __launch_bounds__(256) k_pair_len(const __grid_constant__ QueryC
 // one per visited leaf, so a warp flushes its array into the global 64-bit one
 // before 2^31 leaves have been added to it, and the block sums its warps'
 // arrays into the global one at the end.  The count, the minimum and the
-// maximum come from the finished histogram (k_len_finalize).
+// maximum come from the finished histogram (k_len_finalize).  FDIV: the
+// quotient by lcm is one multiply-high (QueryConst::fdiv).
+template <bool FDIV>
 struct HistCons {
     const int2* TL;
     uint32_t* Dw;  // this warp's difference array (wrapping 32-bit)
@@ -280,7 +283,7 @@ struct HistCons {
     FS_D bool chunk(const QueryConst& q, int, bool valid, int32_t r, int32_t a, int32_t lp)
     {
         if (valid) {
-            const uint32_t qq = div32((uint32_t)r, q.dv_lcm);
+            const uint32_t qq = FDIV ? __umulhi((uint32_t)r, q.lcm_m1) : div32((uint32_t)r, q.dv_lcm);
             const int32_t w = r - (int32_t)(qq * q.lcm);
             const int2 t = TL[w];
             const int32_t lpa = lp + a;
@@ -302,6 +305,7 @@ static int hist_smem_bytes(const QueryConst& q, int threads)
     return (int)q.lcm * 8 + (threads / 32) * ((q.dbins + 31) & ~31) * 4;
 }
 
+template <bool FDIV>
 __global__ void __launch_bounds__(256) k_pair_hist(const __grid_constant__ QueryConst q,
                                                    Scratch sc, int queue)
 {
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(256) k_pair_hist(const __grid_constant__ Query
         TL[w] = t;
     }
     __syncthreads();
-    HistCons cons{TL,      D0 + wid * dstride, sc.D, q.delta < 0 ? q.v : q.u, q.delta < 0 ? q.u : q.v,
+    HistCons<FDIV> cons{TL,      D0 + wid * dstride, sc.D, q.delta < 0 ? q.v : q.u, q.delta < 0 ? q.u : q.v,
                   (uint32_t)q.dbins, 0u, sc.ctr};
     run_queue(q, sq, sc, queue, cons);
     __syncthreads();
@@ -862,13 +866,15 @@ static cudaError_t go(void (*kern)(KArgs...), dim3 g, dim3 b, int smem, cudaStre
     return cudaGetLastError();
 }
 
-// The count walk's instance for q: table path or not, 32-bit group sums or not.
+// The count walk's instance for q: table path or not, 32-bit group sums or
+// not, the quotient by lcm as one multiply-high or not.
 using CountKernel = void (*)(QueryConst, Scratch, int, uint64_t*);
 template <bool PER_SLICE>
 static CountKernel count_kernel(const QueryConst& q, bool tab)
 {
     if (!tab) return k_pair_count<false, PER_SLICE, false>;
-    return q.acc32 ? k_pair_count<true, PER_SLICE, true> : k_pair_count<true, PER_SLICE, false>;
+    if (!q.acc32) return k_pair_count<true, PER_SLICE, false>;
+    return q.fdiv ? k_pair_count<true, PER_SLICE, true, true> : k_pair_count<true, PER_SLICE, true>;
 }
 
 cudaError_t pair_occupancy(const QueryConst& q, Op op, int threads, int elem_bytes, int* nb)
@@ -881,7 +887,7 @@ cudaError_t pair_occupancy(const QueryConst& q, Op op, int threads, int elem_byt
     case OP_SLICES:
         return occ(count_kernel<true>(q, tab), threads, smem, nb);
     case OP_LEN:
-        if (hist_per_warp(q, threads)) return occ(k_pair_hist, threads, smem, nb);
+        if (hist_per_warp(q, threads)) return occ(q.fdiv ? k_pair_hist<true> : k_pair_hist<false>, threads, smem, nb);
         if (q.dbins <= 4096)
             return tab ? occ(k_pair_len<true, true>, threads, smem, nb)
                        : occ(k_pair_len<false, true>, threads, smem, nb);
@@ -909,7 +915,8 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
     case OP_SLICES:
         return go(count_kernel<true>(q, tab), g, b, smem, st, q, sc, queue, (uint64_t*)nullptr);
     case OP_LEN:
-        if (hist_per_warp(q, lc.threads)) return go(k_pair_hist, g, b, smem, st, q, sc, queue);
+        if (hist_per_warp(q, lc.threads))
+            return go(q.fdiv ? k_pair_hist<true> : k_pair_hist<false>, g, b, smem, st, q, sc, queue);
         if (q.dbins <= 4096)
             return tab ? go(k_pair_len<true, true>, g, b, smem, st, q, sc, queue)
                        : go(k_pair_len<false, true>, g, b, smem, st, q, sc, queue);

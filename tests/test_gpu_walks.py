@@ -180,3 +180,43 @@ def test_trailing_walks_sibling_stride_even(walk):
             assert sum(counts) == expect, (n, g, method)
         mm = oracle.minmax_dp(n, g) or (0, 0)
         assert fs.fs_length_stats(n, g, None, cfg(w, fs.METHOD_TRIPLE)) == (expect,) + tuple(mm)
+
+
+@pytest.mark.parametrize("n", [262160, 262161])
+def test_pair_count_quotient_by_lcm_near_the_multiply_high_limit(n):
+    """The PAIR count walk takes floor(r / lcm) as one multiply-high while
+    n lcm < 2^32 and by the general division above it: lcm(127, 129) = 16383,
+    so n = 262160 is the last inside and n = 262161 the first outside."""
+    for g in ((100003, 127, 129, 131), (100003, 127, 129)):
+        expect = oracle.count_dp(n, g)
+        assert fs.fs_count(n, g, cfg(fs.WALK_AUTO)) == expect, (n, g)
+        assert fs.fs_count(n, g, cfg(fs.WALK_LANES)) == expect, (n, g)
+
+
+def brute_hist(n, g):
+    """Histogram of sum a_i over Z(n, g) for g = (huge, c, a, b) with huge > n:
+    every factorization has a_0 = 0; the rest by direct summation."""
+    big, c, a, b = g
+    assert big > n
+    h = np.zeros(n // min(g) + 1, dtype=np.uint64)
+    for k in range(n // c + 1):
+        r = n - k * c
+        x = np.arange(r // a + 1, dtype=np.int64)
+        y, rem = np.divmod(r - a * x, b)
+        ok = rem == 0
+        np.add.at(h, k + x[ok] + y[ok], 1)
+    return h
+
+
+@pytest.mark.parametrize("n", [1398101, 1398112])
+def test_pair_histogram_quotient_by_lcm_near_the_multiply_high_limit(n):
+    """The same for the histogram walk with per-warp difference arrays (pair
+    tables up to lcm 4096, the arrays of a block within 64 KB): lcm(1536,
+    3072) = 3072, n = 1398101 the last inside, n = 1398112 outside; every
+    bin against direct summation."""
+    g = (2000003, 3083, 3072, 1536)
+    ref = brute_hist(n, g)
+    hist = torch.zeros(ref.size, dtype=torch.int64, device="cuda")
+    got = fs.fs_length_stats(n, g, hist, cfg(fs.WALK_AUTO))
+    assert got[0] == int(ref.sum()) == oracle.count_dp(n, g)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref), n
