@@ -650,7 +650,8 @@ cudaError_t call_walk(Call& c, Op op, int queue, const PredConst* pred, void* ou
                       int eb)
 {
     if (c.method == FS_METHOD_TRIPLE) {
-        ProfScope ps(walk_name(op, c.trail == 4 ? FS_METHOD_QUAD : FS_METHOD_TRIPLE), c.st, 1);
+        ProfScope ps(walk_name(op, c.trail == 4 ? FS_METHOD_QUAD : FS_METHOD_TRIPLE), c.st,
+                     triple_walk_kernels(c.q3, op));
         return launch_triple(c.q3, c.sc, op, c.lc, queue, c.T3, c.MN3, c.MX3,
                              op == OP_COUNT ? (uint64_t*)out : nullptr, c.st);
     }

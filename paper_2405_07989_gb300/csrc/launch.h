@@ -55,6 +55,8 @@ cudaError_t launch_pair(const QueryConst& q, const Scratch& sc, Op op, const Lau
 // OP_LEN = count + min / max length)
 // The trailing-table walk: its block size for q3 / op, and blocks per SM.
 int triple_threads(const QueryConst& q3, Op op);
+// Kernels launch_triple enqueues for op (2 for a length range in shared memory).
+int triple_walk_kernels(const QueryConst& q3, Op op);
 cudaError_t triple_occupancy(const QueryConst& q3, Op op, int threads, int* blocks_per_sm);
 // Enumerate's first walk, run by run (k_pair_slice_runs): per-slice counts,
 // the two-level offsets of Scratch::blk, the total (ctr[CTR_TOTAL] and, if

@@ -451,10 +451,15 @@ __global__ void __launch_bounds__(256, 4) k_pair_any(const __grid_constant__ Que
 // The walk runs over the prefixes of the first D-3 levels (the reduced query
 // q3 has one prefix level fewer); the leaf with residual r contributes
 // T3[r] factorizations with lengths lp + a + [MN3[r], MX3[r]].
+// MODE 0: the count; 1: count, minimum and maximum length; 2: minimum and
+// maximum only.  With SMEMT the length range comes from a shared-memory table
+// MM packing MN3[r] (low 16 bits, 0xffff: no completion) and MX3[r] (high 16
+// bits) per residual (MODE 2 always).
 template <int MODE, bool PER_SLICE, bool SMEMT, bool STAG_ = false>
 struct TripleCons {
     const uint64_t* T3;
     const uint32_t* T32;  // SMEMT: shared-memory uint32 copy of T3, or NULL
+    const uint32_t* MM;   // SMEMT, MODE 1 / 2: the packed length range in shared memory
     const int32_t* MN3;
     const int32_t* MX3;
     uint64_t* slice_cnt;
@@ -465,7 +470,7 @@ struct TripleCons {
     static constexpr bool SKIP = false;
     static constexpr bool ANY_ORDER = true;
     static constexpr bool MULTI_SET = true;
-    static constexpr uint32_t CHUNK_OPS = MODE ? 12 : 4;
+    static constexpr uint32_t CHUNK_OPS = MODE == 1 ? 12 : MODE == 2 ? 6 : 4;
     static constexpr bool R_INDEXED = true;
     static constexpr bool STAG = STAG_;  // staggered lanes (walk_slice_packed)
     FS_D void fault() { flag_fault(ctr); }
@@ -482,6 +487,17 @@ struct TripleCons {
     }
     FS_D bool chunk(const QueryConst&, int, bool valid, int32_t r, int32_t a, int32_t lp)
     {
+        if (MODE == 2) {
+            if (valid) {
+                const uint32_t v = MM[r];
+                const int32_t lo = (int32_t)(v & 0xffffu);
+                if (lo != 0xffff) {
+                    mn = min(mn, lp + a + lo);
+                    mx = max(mx, lp + a + (int32_t)(v >> 16));
+                }
+            }
+            return false;
+        }
         if (valid) {
             uint64_t c;
             if constexpr (SMEMT)
@@ -490,8 +506,14 @@ struct TripleCons {
                 c = __ldg(&T3[r]);
             acc += c;
             if (MODE && c) {
-                mn = min(mn, lp + a + __ldg(&MN3[r]));
-                mx = max(mx, lp + a + __ldg(&MX3[r]));
+                if constexpr (SMEMT) {
+                    const uint32_t v = MM[r];
+                    mn = min(mn, lp + a + (int32_t)(v & 0xffffu));
+                    mx = max(mx, lp + a + (int32_t)(v >> 16));
+                } else {
+                    mn = min(mn, lp + a + __ldg(&MN3[r]));
+                    mx = max(mx, lp + a + __ldg(&MX3[r]));
+                }
             }
         }
         return false;
@@ -500,7 +522,7 @@ struct TripleCons {
 
 // SMEMT: the count table is copied to shared memory as uint32 (when its
 // largest entry, recorded by the precompute, fits), so the lookups of the walk
-// hit shared memory instead of L2.
+// hit shared memory instead of L2; for MODE 2 the packed length range.
 template <int MODE, bool PER_SLICE, bool SMEMT, bool STAG = false>
 __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_walk(
     const __grid_constant__ QueryConst q3, Scratch sc, int queue, const uint64_t* T3,
@@ -521,9 +543,18 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_wa
         bmax = -1;
     }
     uint32_t* T32 = nullptr;
-    if (SMEMT && sc.ctr[CTR_TMAX] <= 0xffffffffull) {
+    uint32_t* MM = nullptr;
+    const uint32_t len = (uint32_t)q3.n + 1;
+    if (SMEMT && MODE) {  // MODE 1: after the count table; MODE 2: alone
+        MM = (uint32_t*)dyn + (MODE == 1 ? len : 0);
+        for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
+            const int32_t lo = __ldg(&MN3[p]), hi = __ldg(&MX3[p]);
+            MM[p] = lo >= 0xffff ? 0xffffu : (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+    }
+    if (SMEMT && MODE != 2 && sc.ctr[CTR_TMAX] <= 0xffffffffull) {
         T32 = (uint32_t*)dyn;
-        const uint32_t len = (uint32_t)q3.n + 1, bd = blockDim.x;
+        const uint32_t bd = blockDim.x;
         for (uint32_t p = threadIdx.x; p < len; p += 4 * bd) {  // four loads in flight
             uint64_t v[4];
 #pragma unroll
@@ -534,7 +565,7 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_wa
         }
     }
     __syncthreads();
-    TripleCons<MODE, PER_SLICE, SMEMT, STAG> cons{T3, T32, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
+    TripleCons<MODE, PER_SLICE, SMEMT, STAG> cons{T3, T32, MM, MN3, MX3, sc.slice_cnt, sc.ctr, 0, 0, 0x7fffffff, -1};
     run_queue(q3, sq, sc, queue, cons);
     const uint64_t v = warp_sum_u64(cons.total);
     int mn = cons.mn, mx = cons.mx;
@@ -552,7 +583,10 @@ __global__ void __launch_bounds__(SMEMT ? 1024 : 256, SMEMT ? 1 : 4) k_triple_wa
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (bsum > 0) {
+        if (MODE == 2 && bmax >= 0) {
+            atomicMax((unsigned long long*)&sc.ctr[CTR_MINC], (unsigned long long)(0xffffffffu - (uint32_t)bmin));
+            atomicMax((unsigned long long*)&sc.ctr[CTR_MAX], (unsigned long long)(uint32_t)bmax);
+        } else if (MODE != 2 && bsum > 0) {
             atomicAdd((unsigned long long*)&sc.ctr[CTR_COUNT], bsum);
             if (MODE) {
                 atomicMax((unsigned long long*)&sc.ctr[CTR_MINC], (unsigned long long)(0xffffffffu - (uint32_t)bmin));
@@ -735,14 +769,32 @@ cudaError_t launch_plan_runs(const QueryConst& q, const Scratch& sc, uint64_t S_
 }
 
 // The count modes keep a uint32 copy of the table in shared memory up to
-// this size; above it (or for the length range) the walk reads the uint64
-// table through L2.
+// this size; above it the walk reads the uint64 table through L2.  Where the
+// lengths fit 16 bits the length range keeps its tables in shared memory too:
+// the count table and the packed range in one walk (MODE 1) while both fit,
+// else two walks, the count (MODE 0) and the range alone (MODE 2); beyond
+// that one walk reading all three tables through L2.
 constexpr int TRIPLE_SMEM_MAX = 160 * 1024;
 
 static int triple_smem(const QueryConst& q3, Op op)
 {
     const long long b = ((long long)q3.n + 1) * 4;
-    return (op != OP_LEN && b <= TRIPLE_SMEM_MAX) ? (int)b : 0;
+    if (b > TRIPLE_SMEM_MAX) return 0;
+    if (op != OP_LEN) return (int)b;
+    if (q3.maxlen > 0xfffe) return 0;
+    return 2 * b <= TRIPLE_SMEM_MAX ? (int)(2 * b) : (int)b;
+}
+
+// The length range in two walks (count, then range) rather than one.
+static bool triple_len_split(const QueryConst& q3)
+{
+    const int smem = triple_smem(q3, OP_LEN);
+    return smem && (long long)smem < 2 * ((long long)q3.n + 1) * 4;
+}
+
+int triple_walk_kernels(const QueryConst& q3, Op op)
+{
+    return op == OP_LEN && triple_len_split(q3) ? 2 : 1;
 }
 
 int triple_threads(const QueryConst& q3, Op op)
@@ -767,15 +819,15 @@ static bool triple_staggers(const QueryConst& q3)
     return (hsib & 1) == 0 && (hin & 1) == 1;
 }
 
-template <bool PER_SLICE, bool STAG>
+template <int MODE, bool PER_SLICE, bool STAG>
 static cudaError_t launch_triple_smem(const QueryConst& q3, const Scratch& sc, dim3 g, dim3 b,
-                                      int smem, int queue, const uint64_t* T3, uint64_t* dev_count,
-                                      cudaStream_t st)
+                                      int smem, int queue, const uint64_t* T3, const int32_t* MN3,
+                                      const int32_t* MX3, uint64_t* dev_count, cudaStream_t st)
 {
-    const cudaError_t e = smem_optin((const void*)k_triple_walk<0, PER_SLICE, true, STAG>, smem);
+    const cudaError_t e = smem_optin((const void*)k_triple_walk<MODE, PER_SLICE, true, STAG>, smem);
     if (e == cudaSuccess)
-        k_triple_walk<0, PER_SLICE, true, STAG><<<g, b, smem, st>>>(q3, sc, queue, T3, nullptr,
-                                                                   nullptr, dev_count);
+        k_triple_walk<MODE, PER_SLICE, true, STAG><<<g, b, smem, st>>>(q3, sc, queue, T3, MN3, MX3,
+                                                                      dev_count);
     return e;
 }
 
@@ -790,21 +842,34 @@ cudaError_t launch_triple(const QueryConst& q3, const Scratch& sc, Op op, const 
     switch (op) {
     case OP_COUNT:
         if (smem) {
-            e = stag ? launch_triple_smem<false, true>(q3, sc, g, b, smem, queue, T3, dev_count, st)
-                     : launch_triple_smem<false, false>(q3, sc, g, b, smem, queue, T3, dev_count, st);
+            e = stag ? launch_triple_smem<0, false, true>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, dev_count, st)
+                     : launch_triple_smem<0, false, false>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, dev_count, st);
         } else {
             k_triple_walk<0, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, dev_count);
         }
         break;
     case OP_SLICES:
         if (smem) {
-            e = stag ? launch_triple_smem<true, true>(q3, sc, g, b, smem, queue, T3, nullptr, st)
-                     : launch_triple_smem<true, false>(q3, sc, g, b, smem, queue, T3, nullptr, st);
+            e = stag ? launch_triple_smem<0, true, true>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, nullptr, st)
+                     : launch_triple_smem<0, true, false>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, nullptr, st);
         } else {
             k_triple_walk<0, true, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
         }
         break;
-    case OP_LEN: k_triple_walk<1, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr); break;
+    case OP_LEN:
+        if (smem && triple_len_split(q3)) {  // the count, then the range (its own slice queue)
+            e = stag ? launch_triple_smem<0, false, true>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, nullptr, st)
+                     : launch_triple_smem<0, false, false>(q3, sc, g, b, smem, queue, T3, nullptr, nullptr, nullptr, st);
+            if (e == cudaSuccess)
+                e = stag ? launch_triple_smem<2, false, true>(q3, sc, g, b, smem, CTR_QUEUE2, T3, MN3, MX3, nullptr, st)
+                         : launch_triple_smem<2, false, false>(q3, sc, g, b, smem, CTR_QUEUE2, T3, MN3, MX3, nullptr, st);
+        } else if (smem) {
+            e = stag ? launch_triple_smem<1, false, true>(q3, sc, g, b, smem, queue, T3, MN3, MX3, nullptr, st)
+                     : launch_triple_smem<1, false, false>(q3, sc, g, b, smem, queue, T3, MN3, MX3, nullptr, st);
+        } else {
+            k_triple_walk<1, false, false><<<g, b, 0, st>>>(q3, sc, queue, T3, MN3, MX3, nullptr);
+        }
+        break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

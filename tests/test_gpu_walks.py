@@ -220,3 +220,17 @@ def test_pair_histogram_quotient_by_lcm_near_the_multiply_high_limit(n):
     got = fs.fs_length_stats(n, g, hist, cfg(fs.WALK_AUTO))
     assert got[0] == int(ref.sum()) == oracle.count_dp(n, g)
     assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref), n
+
+
+@pytest.mark.parametrize("walk", ["auto", "lanes"])
+def test_trailing_length_range_both_paths(walk):
+    """The length range from the trailing tables: two walks with the tables in
+    shared memory (the count, then minimum and maximum packed in 16 bits) while
+    the table fits 160 KB, one walk through L2 above (n >= 40960).  Count,
+    minimum and maximum against the oracle's DPs, both sides of that size."""
+    w = WALKS[walk]
+    for n in (3000, 40959, 40960, 45000):
+        for g in ((97, 89, 83, 79, 73), (64, 61, 59, 53, 47, 43), (124, 95, 89, 61, 56, 52)):
+            expect = (oracle.count_dp(n, g),) + tuple(oracle.minmax_dp(n, g) or (0, 0))
+            for method in (fs.METHOD_TRIPLE, fs.METHOD_QUAD, fs.METHOD_AUTO):
+                assert fs.fs_length_stats(n, g, None, cfg(w, method)) == expect, (n, g, method)
