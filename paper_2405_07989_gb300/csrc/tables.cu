@@ -33,7 +33,7 @@ namespace fsi {
 // run l0 + t delta); the sums over a are strided scans: a running sum, and a
 // running min / max of (bound - floor(p/h)) plus floor(p/h).  k = 4 adds level
 // P-2 the same way: T4[p] = sum_{b >= 0} T3[p - b h_{P-2}], and so on for the
-// length range.  One block each.
+// length range.  One block per table (the count, the minimum, the maximum).
 struct PrecompArgs {
     QueryConst qw;  // the query the walk runs over
     QueryConst qt;  // the query whose trailing tables are built (trail_k > 0)
@@ -47,9 +47,9 @@ struct PrecompArgs {
     uint64_t* tmax;  // the trailing table's largest entry (ctr[CTR_TMAX])
     int32_t trail_k;
     int32_t nroles;
-    int32_t role[4];
+    int32_t role[6];
 };
-enum { ROLE_WEIGHTS = 0, ROLE_PAIRTAB = 1, ROLE_TRAIL = 2 };
+enum { ROLE_WEIGHTS = 0, ROLE_PAIRTAB = 1, ROLE_TRAIL = 2, ROLE_TRAIL_MN = 3, ROLE_TRAIL_MX = 4 };
 
 __global__ void __launch_bounds__(1024) k_precompute(const __grid_constant__ PrecompArgs a)
 {
@@ -69,7 +69,13 @@ __global__ void __launch_bounds__(1024) k_precompute(const __grid_constant__ Pre
         pair_tables_fill(a.qw, a.E, a.X0, a.YD, threadIdx.x, blockDim.x);
         break;
     case ROLE_TRAIL:
-        trailing_tables_block(a.qt, a.trail_k, a.T, a.MN, a.MX, part64, part32, a.tmax);
+        trailing_tables_block(a.qt, a.trail_k, a.T, nullptr, nullptr, part64, part32, a.tmax);
+        break;
+    case ROLE_TRAIL_MN:
+        trailing_tables_block(a.qt, a.trail_k, nullptr, a.MN, nullptr, part64, part32);
+        break;
+    case ROLE_TRAIL_MX:
+        trailing_tables_block(a.qt, a.trail_k, nullptr, nullptr, a.MX, part64, part32);
         break;
     }
 }
@@ -333,7 +339,11 @@ cudaError_t launch_precompute(const QueryConst& q, const Scratch& sc, cudaStream
     a.trail_k = trail_k;
     if (q.nw > 0) a.role[a.nroles++] = ROLE_WEIGHTS;
     if (q.tab_e || q.tab_xy) a.role[a.nroles++] = ROLE_PAIRTAB;
-    if (qt && trail_k > 0) a.role[a.nroles++] = ROLE_TRAIL;
+    if (qt && trail_k > 0) {
+        a.role[a.nroles++] = ROLE_TRAIL;
+        if (MN) a.role[a.nroles++] = ROLE_TRAIL_MN;
+        if (MX) a.role[a.nroles++] = ROLE_TRAIL_MX;
+    }
     if (a.nroles == 0) return cudaSuccess;
     k_precompute<<<a.nroles, 1024, 0, st>>>(a);
     return cudaGetLastError();

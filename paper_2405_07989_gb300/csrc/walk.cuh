@@ -1200,6 +1200,19 @@ FS_D void flag_fault(uint64_t* ctr)
 //   y0 = q u + YD[w].
 // General path: the same quantities by division.
 // ---------------------------------------------------------------------------
+// The smallest x of the pair's solutions from t = (r / G) mod v: t u^-1 mod v.
+// Below v = 46341 the product t inv < v^2 stays under 2^31 and the remainder
+// is one invariant division; above, a 64-bit remainder.
+template <class QC>
+FS_D uint32_t pair_x0(const QC& q, uint32_t t)
+{
+    if (q.v < 46341) {
+        const uint32_t pr = t * (uint32_t)q.inv;
+        return pr - div32(pr, q.dv_v) * (uint32_t)q.v;
+    }
+    return (uint32_t)(((uint64_t)t * (uint32_t)q.inv) % (uint32_t)q.v);
+}
+
 template <bool TAB, class QC>
 FS_D uint32_t pair_count(const QC& q, const int8_t* E, int32_t r)
 {
@@ -1212,7 +1225,7 @@ FS_D uint32_t pair_count(const QC& q, const int8_t* E, int32_t r)
         uint32_t rg = div32((uint32_t)r, q.dv_G);
         if ((int32_t)rg * q.G != r) return 0u;
         uint32_t t = rg - div32(rg, q.dv_v) * (uint32_t)q.v;
-        uint32_t x0 = (uint32_t)(((uint64_t)t * (uint32_t)q.inv) % (uint32_t)q.v);
+        uint32_t x0 = pair_x0(q, t);
         uint32_t xmax = div32((uint32_t)r, q.dv_A);
         return xmax >= x0 ? div32(xmax - x0, q.dv_v) + 1u : 0u;
     }
@@ -1235,7 +1248,7 @@ FS_D uint32_t pair_xy(const QC& q, const int32_t* X0, const int32_t* YD, int32_t
         uint32_t rg = div32((uint32_t)r, q.dv_G);
         if ((int32_t)rg * q.G != r) return 0u;
         uint32_t t = rg - div32(rg, q.dv_v) * (uint32_t)q.v;
-        uint32_t xx = (uint32_t)(((uint64_t)t * (uint32_t)q.inv) % (uint32_t)q.v);
+        uint32_t xx = pair_x0(q, t);
         uint32_t xmax = div32((uint32_t)r, q.dv_A);
         if (xmax < xx) return 0u;
         x0 = (int32_t)xx;
@@ -1297,54 +1310,49 @@ FS_D PairC pair_consts(const QueryConst& q)
 // The trailing-k tables of q (k = 3 or 4) for p = 0..n, built by the calling
 // block (any size; part64 / part32 hold blockDim.x entries).  Level P-1 is
 // summed over the pair's closed form; each further level (P-2 for k = 4) is
-// one more strided scan of the same tables in place (the TRAIL role of
-// k_precompute).
+// one more strided scan of the same tables in place (the TRAIL roles of
+// k_precompute).  Any of T, MN, MX may be NULL: k_precompute builds each on a
+// block of its own.
 // tmax (nullable, global): receives the largest entry of T (atomicMax).
 FS_D void trailing_tables_block(const QueryConst& q, int k, uint64_t* T, int32_t* MN, int32_t* MX,
                                 uint64_t* part64, int32_t* part32, uint64_t* tmax = nullptr)
 {
     const int len = q.n + 1;
+    const bool lens = MN || MX;
     for (int lvl = q.P - 1; lvl >= q.P + 2 - k; lvl--) {
         const int h = q.h[lvl];
         const Div32 dvh = q.dv_h[lvl];
         for (int p = threadIdx.x; p < len; p += blockDim.x) {
             const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-            if (lvl == q.P - 1 && !MN) {
+            if (lvl == q.P - 1 && !lens) {
                 T[p] = pair_count<false>(q, (const int8_t*)nullptr, p);
             } else if (lvl == q.P - 1) {
                 int32_t x0 = 0, y0 = 0;
                 const uint32_t c =
                     pair_xy<false>(q, (const int32_t*)nullptr, (const int32_t*)nullptr, p, x0, y0);
-                T[p] = c;
-                {
-                    if (c > 0) {
-                        const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
-                        MN[p] = min(l0, l1) - t;
-                        MX[p] = max(l0, l1) - t;
-                    } else {
-                        MN[p] = TRIPLE_NONE - t;
-                        MX[p] = -TRIPLE_NONE - t;
-                    }
-                }
-            } else if (MN) {
-                MN[p] -= t;
-                MX[p] -= t;
+                if (T) T[p] = c;
+                const int32_t l0 = x0 + y0, l1 = l0 + (int32_t)(c - 1) * q.delta;
+                if (MN) MN[p] = (c > 0 ? min(l0, l1) : TRIPLE_NONE) - t;
+                if (MX) MX[p] = (c > 0 ? max(l0, l1) : -TRIPLE_NONE) - t;
+            } else {
+                if (MN) MN[p] -= t;
+                if (MX) MX[p] -= t;
             }
         }
         __syncthreads();
-        block_strided_scan<uint64_t>(T, len, h, part64, (uint64_t)0, OpAdd());
-        if (MN) {
-            block_strided_scan<int32_t>(MN, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
-            block_strided_scan<int32_t>(MX, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+        if (T) block_strided_scan<uint64_t>(T, len, h, part64, (uint64_t)0, OpAdd());
+        if (MN) block_strided_scan<int32_t>(MN, len, h, part32, (int32_t)TRIPLE_NONE, OpMin());
+        if (MX) block_strided_scan<int32_t>(MX, len, h, part32, (int32_t)-TRIPLE_NONE, OpMax());
+        if (lens) {
             for (int p = threadIdx.x; p < len; p += blockDim.x) {
                 const int32_t t = (int32_t)div32((uint32_t)p, dvh);
-                MN[p] += t;
-                MX[p] += t;
+                if (MN) MN[p] += t;
+                if (MX) MX[p] += t;
             }
         }
         __syncthreads();
     }
-    if (tmax) {
+    if (tmax && T) {
         uint64_t m = 0;
         for (int p = threadIdx.x; p < len; p += blockDim.x) m = T[p] > m ? T[p] : m;
         for (int o = 16; o > 0; o >>= 1) {

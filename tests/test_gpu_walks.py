@@ -234,3 +234,33 @@ def test_trailing_length_range_both_paths(walk):
             expect = (oracle.count_dp(n, g),) + tuple(oracle.minmax_dp(n, g) or (0, 0))
             for method in (fs.METHOD_TRIPLE, fs.METHOD_QUAD, fs.METHOD_AUTO):
                 assert fs.fs_length_stats(n, g, None, cfg(w, method)) == expect, (n, g, method)
+
+
+def brute_count_minmax3(n, g):
+    """|Z(n, g)| and its length range for three generators by direct
+    summation: every (a, x) with the third coordinate solved (numpy)."""
+    g0, g1, g2 = g
+    c, lo, hi = 0, None, None
+    x = np.arange(n // g1 + 1, dtype=np.int64)
+    for a in range(n // g0 + 1):
+        rest = n - a * g0 - x * g1
+        ok = (rest >= 0) & (rest % g2 == 0)
+        if ok.any():
+            tot = a + x[ok] + rest[ok] // g2
+            c += int(ok.sum())
+            lo = int(tot.min()) if lo is None else min(lo, int(tot.min()))
+            hi = int(tot.max()) if hi is None else max(hi, int(tot.max()))
+    return c, (lo, hi) if c else (0, 0)
+
+
+@pytest.mark.parametrize("g", [(99991, 70001, 50021), (99991, 70001, 46337)])
+def test_pair_first_solution_both_remainder_paths(g):
+    """Without pair tables (lcm above the table limit) a leaf's first solution
+    is t u^-1 mod v: one invariant division while v^2 < 2^31 (v = 46337
+    here), a 64-bit remainder above (v = 50021).  Count and length range of
+    the PAIR walk at n = 2e9 against direct summation."""
+    n = 2_000_000_011
+    c, mm = brute_count_minmax3(n, g)
+    assert c > 1000
+    assert fs.fs_count(n, g, cfg(fs.WALK_AUTO)) == c, g
+    assert fs.fs_length_stats(n, g, None, cfg(fs.WALK_AUTO)) == (c,) + mm, g
