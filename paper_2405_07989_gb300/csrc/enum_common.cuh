@@ -49,6 +49,9 @@ struct Stager {
     FS_D ELEM* stg() const { return (ELEM*)wbase; }
     FS_D ELEM* cursor() const { return stg() + phase + nst * d; }
     FS_D bool fits(int rows) const { return phase + (nst + rows) * d <= STG; }
+    // rows that still fit the buffer (D: the row width, d, as a constant)
+    template <int D>
+    FS_D uint32_t room() const { return (uint32_t)((STG - phase) / D - nst); }
     // window position of the first staged element (negative: before the window)
     FS_D int64_t wpos() const { return (int64_t)(row_base * (uint64_t)d) - (int64_t)lo_elems; }
 

@@ -27,7 +27,6 @@ struct EnumFix {
     const uint64_t* slice_off;
     const uint64_t* blk;
     uint64_t* ctr;
-    int32_t piece;
     int32_t pre[NP > 0 ? NP : 1];
     int32_t a2base, lpbase;  // level P-2 and prefix sum of the sibling group's first run
 
@@ -85,9 +84,13 @@ struct EnumFix {
     FS_D void emit_one(const QueryConst& q, int lane, uint32_t cs, int32_t xs, int32_t ys,
                        int32_t as, int32_t a2s)
     {
-        for (uint32_t t0 = 0; t0 < cs; t0 += (uint32_t)piece) {
-            const uint32_t npc = min((uint32_t)piece, cs - t0);
-            if (!sg.fits((int)npc)) sg.flush();
+        for (uint32_t t0 = 0; t0 < cs;) {
+            uint32_t room = sg.template room<D>();
+            if (room == 0) {
+                sg.flush();
+                room = sg.template room<D>();
+            }
+            const uint32_t npc = min(room, cs - t0);
             ELEM* sb = sg.cursor();
             for (uint32_t j = 0; j < npc; j += 32) {
                 const uint32_t k = j + lane;
@@ -97,6 +100,7 @@ struct EnumFix {
                 }
             }
             sg.nst += (int32_t)npc;
+            t0 += npc;
         }
     }
 
@@ -125,16 +129,22 @@ struct EnumFix {
         }
         const uint32_t T = __shfl_sync(FULL, incl, 31);
         const uint32_t excl = incl - c;
-        for (uint32_t ps = 0; ps < T; ps += (uint32_t)piece) {
-            const uint32_t npc = min((uint32_t)piece, T - ps);
-            if (!sg.fits((int)npc)) sg.flush();
+        // the rows fill the staging buffer to its end before it is flushed
+        for (uint32_t ps = 0; ps < T;) {
+            uint32_t room = sg.template room<D>();
+            if (room == 0) {
+                sg.flush();
+                room = sg.template room<D>();
+            }
+            const uint32_t npc = min(room, T - ps);
             ELEM* sb = sg.cursor();
-            // this lane's rows of the piece [ps, ps + npc): t = i - excl of its leaf
+            // this lane's rows of [ps, ps + npc): t = i - excl of its leaf
             const uint32_t lo = max(excl, ps), hi = min(incl, ps + npc);
             int32_t t = (int32_t)(lo - excl);
             for (uint32_t i = lo; i < hi; i++, t++)
                 put_row(sb + (i - ps) * D, a2, a, x0 + t * q.v, y0 - t * q.u);
             sg.nst += (int32_t)npc;
+            ps += npc;
         }
         return false;
     }
@@ -170,7 +180,6 @@ __global__ void __launch_bounds__(256, 4) k_pair_enum_fix(const __grid_constant_
     cons.slice_off = sc.slice_off;
     cons.blk = sc.blk;
     cons.ctr = sc.ctr;
-    cons.piece = (Stager<ELEM>::STG - Stager<ELEM>::VEC) / D;
 #pragma unroll
     for (int k = 0; k < C::NP; k++) cons.pre[k] = 0;
     cons.a2base = 0;
