@@ -196,6 +196,10 @@ FS_D void warp_chains_scan2(InA ina, uint64_t* outa, InB inb, uint64_t* outb, in
     __syncthreads();
 }
 
+// Elements a thread of the segmented scans loads before it combines them: the
+// loads of a segment are independent, the running sum is not.
+constexpr int SCAN_BATCH = 8;
+
 FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint64_t* out, int len,
                                    int s, uint64_t* part)
 {
@@ -214,9 +218,16 @@ FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint6
         int nch = s < len ? s : len;
         for (int rho = tid; rho < nch; rho += T) {
             uint64_t sum = 0;
-            for (int p = rho; p < len; p += s) {
-                sum += sps_in(in, p, dv_in);
-                out[p] = sum;
+            const int cl = (len - 1 - rho) / s + 1;
+            for (int t = 0; t < cl; t += SCAN_BATCH) {
+                uint64_t v[SCAN_BATCH];  // independent loads in flight
+#pragma unroll
+                for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < cl ? sps_in(in, rho + (t + j) * s, dv_in) : 0;
+#pragma unroll
+                for (int j = 0; j < SCAN_BATCH; j++) {
+                    sum += v[j];
+                    if (t + j < cl) out[rho + (t + j) * s] = sum;
+                }
             }
         }
         __syncthreads();
@@ -228,14 +239,16 @@ FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint6
     const int seg = (cl_max + G - 1) / G;
     const int rho = tid % s, g = tid / s;
     const bool act = g < G;
-    int t0 = g * seg, t1 = t0 + seg;
+    const int t0 = g * seg;
+    // this segment's elements t0 .. te-1 of chain rho (te <= t0: none)
+    const int te = act ? min(t0 + seg, (len - 1 - rho) / s + 1) : t0;
     uint64_t sum = 0;
-    if (act) {
-        for (int t = t0; t < t1; t++) {
-            long long p = rho + (long long)t * s;
-            if (p >= len) break;
-            sum += sps_in(in, (int)p, dv_in);
-        }
+    for (int t = t0; t < te; t += SCAN_BATCH) {
+        uint64_t v[SCAN_BATCH];
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < te ? sps_in(in, rho + (t + j) * s, dv_in) : 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) sum += v[j];
     }
     part[tid] = act ? sum : 0;
     __syncthreads();
@@ -247,12 +260,14 @@ FS_D void block_strided_prefix_sum(const uint64_t* in, const Div32& dv_in, uint6
         __syncthreads();
     }
     uint64_t run = (act && g > 0) ? part[tid - s] : 0;  // exclusive prefix of this segment
-    if (act) {
-        for (int t = t0; t < t1; t++) {
-            long long p = rho + (long long)t * s;
-            if (p >= len) break;
-            run += sps_in(in, (int)p, dv_in);
-            out[p] = run;
+    for (int t = t0; t < te; t += SCAN_BATCH) {
+        uint64_t v[SCAN_BATCH];
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < te ? sps_in(in, rho + (t + j) * s, dv_in) : 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) {
+            run += v[j];
+            if (t + j < te) out[rho + (t + j) * s] = run;
         }
     }
     __syncthreads();
@@ -287,9 +302,16 @@ FS_D void block_strided_scan(T* x, int len, int s, T* part, T ident, Op op)
         const int nch = s < len ? s : len;
         for (int rho = tid; rho < nch; rho += NT) {
             T acc = ident;
-            for (int p = rho; p < len; p += s) {
-                acc = op(acc, x[p]);
-                x[p] = acc;
+            const int cl = (len - 1 - rho) / s + 1;
+            for (int t = 0; t < cl; t += SCAN_BATCH) {
+                T v[SCAN_BATCH];  // independent loads in flight
+#pragma unroll
+                for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < cl ? x[rho + (t + j) * s] : ident;
+#pragma unroll
+                for (int j = 0; j < SCAN_BATCH; j++) {
+                    acc = op(acc, v[j]);
+                    if (t + j < cl) x[rho + (t + j) * s] = acc;
+                }
             }
         }
         __syncthreads();
@@ -300,14 +322,16 @@ FS_D void block_strided_scan(T* x, int len, int s, T* part, T ident, Op op)
     const int seg = (cl_max + G - 1) / G;
     const int rho = tid % s, g = tid / s;
     const bool act = g < G;
-    const int t0 = g * seg, t1 = t0 + seg;
+    const int t0 = g * seg;
+    const int te = act ? min(t0 + seg, (len - 1 - rho) / s + 1) : t0;
     T acc = ident;
-    if (act)
-        for (int t = t0; t < t1; t++) {
-            const long long p = rho + (long long)t * s;
-            if (p >= len) break;
-            acc = op(acc, x[p]);
-        }
+    for (int t = t0; t < te; t += SCAN_BATCH) {
+        T v[SCAN_BATCH];
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < te ? x[rho + (t + j) * s] : ident;
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) acc = op(acc, v[j]);
+    }
     part[tid] = act ? acc : ident;
     __syncthreads();
     for (int off = s; off < G * s; off <<= 1) {
@@ -317,13 +341,16 @@ FS_D void block_strided_scan(T* x, int len, int s, T* part, T ident, Op op)
         __syncthreads();
     }
     T run = (act && g > 0) ? part[tid - s] : ident;
-    if (act)
-        for (int t = t0; t < t1; t++) {
-            const long long p = rho + (long long)t * s;
-            if (p >= len) break;
-            run = op(run, x[p]);
-            x[p] = run;
+    for (int t = t0; t < te; t += SCAN_BATCH) {
+        T v[SCAN_BATCH];
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) v[j] = t + j < te ? x[rho + (t + j) * s] : ident;
+#pragma unroll
+        for (int j = 0; j < SCAN_BATCH; j++) {
+            run = op(run, v[j]);
+            if (t + j < te) x[rho + (t + j) * s] = run;
         }
+    }
     __syncthreads();
 }
 
