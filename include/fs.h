@@ -96,7 +96,11 @@ typedef struct fs_config {
                               walk them in descending order, which visits the fewest
                               prefixes; the result is the same set (Z does not depend on
                               the order of the generators, Sec. 1). */
-    int64_t slices;        /* number of lexicographic slices [lo,hi) (Sec. 4); 0 = auto */
+    int64_t slices;        /* number of lexicographic slices [lo,hi) (Sec. 4), of equal leaf
+                              counts; 0 = auto: the planner picks the count from the
+                              leaves and the grid, and the last sixteenth of the slices
+                              hold a sixteenth of a regular slice each (short slices at
+                              the end of the walks' queue) */
     int32_t block_threads; /* threads per block; 0 = auto */
     int32_t blocks_per_sm; /* resident blocks per SM for the persistent grid; 0 = auto */
     int32_t walk;          /* fs_walk: how the order-free consumers (count, length
