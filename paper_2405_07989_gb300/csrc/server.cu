@@ -374,10 +374,13 @@ bool fs_server::step()
             j.bytes = 0;
             j.refuse_hist = false;
             if (q.r.op == FS_REQ_LENGTHS && q.r.hist) {
-                if (hist_walk_leaves(q.r) > (double)cfg.hist_max_leaves)
-                    j.refuse_hist = true;  // count and range only, then FS_E_CAPACITY
+                // a histogram over the work bound or larger than the whole budget:
+                // count and range only, then FS_E_CAPACITY
+                const uint64_t hb = ((uint64_t)q.r.n / min_gen(q.r) + 1) * 8;
+                if (hist_walk_leaves(q.r) > (double)cfg.hist_max_leaves || hb > pool.size)
+                    j.refuse_hist = true;
                 else
-                    j.bytes = ((uint64_t)q.r.n / min_gen(q.r) + 1) * 8;
+                    j.bytes = hb;
             }
             job_wait.push_back(j);
             progress = true;

@@ -313,6 +313,14 @@ def test_server_direct_jobs():
         assert r["status"] == fs.FS_E_CAPACITY and r["rows"] == 0 and r["t_start"] == r["t_job"]
         assert r["count"] == oracle.count_dp(*big)
         assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(*big)
+    # a histogram larger than the whole budget (858 bins of 8 bytes against 4 KB)
+    wide = (6000, (7, 11, 13))
+    with fs.Server(mem_budget_bytes=4096, direct_leaves=1) as srv:
+        tw = srv.submit(fs.REQ_LENGTHS, *wide, hist=True)
+        r = drain(srv, [tw])[tw]
+        assert r["status"] == fs.FS_E_CAPACITY and r["rows"] == 0
+        assert r["count"] == oracle.count_dp(*wide)
+        assert (r["min_len"], r["max_len"]) == oracle.minmax_dp(*wide)
 
 
 def test_server_long_count_runs_direct():
