@@ -489,9 +489,12 @@ def test_config3_count_and_lengths_dp_exact():
 @pytest.mark.parametrize("seed", [1, 2])
 def test_config3_other_seeds(seed):
     n, g = workloads.config3(seed)
-    assert fs.fs_count(n, g) == oracle.count_dp(n, g)
-    assert fs.fs_count(n, g, PAIR) == oracle.count_dp(n, g)
-    assert fs.fs_count(n, g, TRIPLE) == oracle.count_dp(n, g)
+    expect = oracle.count_dp(n, g)
+    assert fs.fs_count(n, g) == expect
+    assert fs.fs_count(n, g, PAIR) == expect
+    assert fs.fs_count(n, g, TRIPLE) == expect
+    # the length range from the trailing tables (count walk, then range walk)
+    assert fs.fs_length_stats(n, g, None) == (expect,) + oracle.minmax_dp(n, g)
 
 
 # ---------------------------------------------------------------------------
