@@ -30,7 +30,7 @@ struct CountCons {
     uint64_t total;  // this lane, all slices
     uint32_t acc32;  // this lane, current group (ACC32)
     uint64_t* ctr;
-    static constexpr int UNROLL = 4;
+    static constexpr int UNROLL = 8;  // full steps per loop trip (4: 1.5 % slower)
     static constexpr bool SKIP = true;
     static constexpr bool ANY_ORDER = true;
     static constexpr bool MULTI_SET = true;
