@@ -899,6 +899,9 @@ def serving_extras(fs, workloads, rate: float, nreq: int, hist: bool = True):
         "by_op": by_op, "stages": stages, "status": status,
         "histograms": sum(1 for r in rs if r["op"] == fs.REQ_LENGTHS and job_of(r)),
         "factorizations_served": int(sum(r["count"] for r in rs if r["status"] == fs.FS_OK)),
+        # the size distribution of the requests' sets |Z| beside the latencies
+        "set_size": {q: float(np.percentile([r["count"] for r in rs], p))
+                     for q, p in (("p50", 50), ("p90", 90), ("p99", 99), ("max", 100))},
     }
 
 
