@@ -814,6 +814,26 @@ def batch_extras(fs, workloads, dev):
     return out
 
 
+def serving_stages(rs):
+    """Per-stage durations (seconds) of served responses: queue (submit to
+    launch), batch (batch launch to its results), direct_job (a count / length
+    request run as a job from the start, t_start = t_job: launch to results),
+    job_wait and job (an enumerate or histogram after its batch), answer (results
+    to the response, requests without a job after the batch)."""
+    ran = [r for r in rs if r["t_start"] > 0]
+    direct_t = {r["ticket"] for r in ran if r["t_job"] > 0 and r["t_start"] == r["t_job"]}
+    direct = [r for r in ran if r["ticket"] in direct_t]
+    batched = [r for r in ran if r["ticket"] not in direct_t]
+    jobs = [r for r in batched if r["t_job"] > 0]
+    return {"queue": [r["t_start"] - r["t_submit"] for r in ran],
+            "batch": [r["t_counted"] - r["t_start"] for r in batched],
+            "direct_job": [r["t_counted"] - r["t_start"] for r in direct],
+            "job_wait": [r["t_job"] - r["t_counted"] for r in jobs],
+            "job": [r["t_done"] - r["t_job"] for r in jobs],
+            "answer": [r["t_done"] - r["t_counted"] for r in ran
+                       if r["t_job"] == 0 or r["ticket"] in direct_t]}
+
+
 def serving_extras(fs, workloads, rate: float, nreq: int, hist: bool = True):
     """The serving workload: Poisson arrivals of queries drawn like the batched
     ones with n up to 20000, 80 % count / 15 % length statistics (with the
@@ -873,19 +893,7 @@ def serving_extras(fs, workloads, rate: float, nreq: int, hist: bool = True):
     for op, name in ((fs.REQ_COUNT, "count"), (fs.REQ_LENGTHS, "lengths"),
                      (fs.REQ_ENUMERATE, "enumerate")):
         by_op[name] = pct([r["t_done"] - r["t_submit"] for r in rs if r["op"] == op])
-    ran = [r for r in rs if r["t_start"] > 0]
-    # direct: a count / length request run as a job from the start (no batch)
-    direct = [r for r in ran if r["t_job"] > 0 and r["t_start"] == r["t_job"]]
-    direct_t = {r["ticket"] for r in direct}
-    batched = [r for r in ran if r["ticket"] not in direct_t]
-    jobs = [r for r in batched if r["t_job"] > 0]
-    stages = {"queue": pct([r["t_start"] - r["t_submit"] for r in ran]),
-              "batch": pct([r["t_counted"] - r["t_start"] for r in batched]),
-              "direct_job": pct([r["t_counted"] - r["t_start"] for r in direct]),
-              "job_wait": pct([r["t_job"] - r["t_counted"] for r in jobs]),
-              "job": pct([r["t_done"] - r["t_job"] for r in jobs]),
-              "answer": pct([r["t_done"] - r["t_counted"] for r in ran
-                             if r["t_job"] == 0 or r["ticket"] in direct_t])}
+    stages = {k: pct(v) for k, v in serving_stages(rs).items()}
     status = {}
     for r in rs:
         status[fs.status_name(r["status"])] = status.get(fs.status_name(r["status"]), 0) + 1

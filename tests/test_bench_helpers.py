@@ -95,3 +95,23 @@ def test_count_roofline_units_are_the_walk_leaves():
     r = bench.count_roofline(_FakeFs, n, g, 2.0, rates)
     assert r["leaves_resolved"] == direct and r["frac"] is None
     assert abs(r["useful_frac"] - direct * bench.COUNT_OPS_PER_LEAF / 2e-3 / 1e12) < 1e-12
+
+
+def test_serving_stages_split_direct_and_batched_requests():
+    """The serving breakdown: a batched count (no job), a batched histogram
+    (job after the batch), a direct count (its job is its launch) and a request
+    never started; every stage non-negative and each request in its stages."""
+    def resp(ticket, sub, start, counted, job, done):
+        return {"ticket": ticket, "t_submit": sub, "t_start": start, "t_counted": counted,
+                "t_job": job, "t_done": done}
+    rs = [resp(1, 0.0, 1.0, 3.0, 0.0, 3.5),     # batched, no job
+          resp(2, 0.0, 1.0, 3.0, 4.0, 9.0),     # batched, then a job
+          resp(3, 0.5, 2.0, 6.0, 2.0, 6.25),    # direct: launched at 2, results at 6
+          resp(4, 0.0, 0.0, 0.0, 0.0, 0.1)]     # refused before it ran
+    st = bench.serving_stages(rs)
+    assert sorted(st["queue"]) == [1.0, 1.0, 1.5]
+    assert sorted(st["batch"]) == [2.0, 2.0]
+    assert st["direct_job"] == [4.0]
+    assert st["job_wait"] == [1.0] and st["job"] == [5.0]
+    assert sorted(st["answer"]) == [0.25, 0.5]
+    assert all(x >= 0 for v in st.values() for x in v)
