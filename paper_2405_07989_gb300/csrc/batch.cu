@@ -14,10 +14,18 @@
 namespace fsi {
 
 // The query a work item walks: q, or for trailing-k queries q with k - 2
-// prefix levels fewer (the last k levels then come from the tables).
-FS_D void batch_walk_query(const BatchQ& B, QueryConst& out)
+// prefix levels fewer (the last k levels then come from the tables).  Copied
+// word by word by the `nt` threads t = 0..nt-1 that call it (a warp or a
+// block; one thread alone would load the whole structure in sequence), then
+// reduced by thread 0; the caller synchronises those threads after it.
+FS_D void batch_walk_query_copy(const BatchQ& B, QueryConst& out, int t, int nt)
 {
-    out = B.q;
+    const uint32_t* src = (const uint32_t*)&B.q;
+    uint32_t* dst = (uint32_t*)&out;
+    for (int w = t; w < (int)(sizeof(QueryConst) / 4); w += nt) dst[w] = src[w];
+}
+FS_D void batch_walk_query_reduce(const BatchQ& B, QueryConst& out)
+{
     if (B.trail) reduce_to_trailing(out, B.trail);
 }
 
@@ -28,7 +36,9 @@ __global__ void __launch_bounds__(256) k_batch_tables(BatchDev b)
     __shared__ QueryConst qw;
     BatchQ& B = b.qs[blockIdx.x];
     if (!B.valid) return;
-    if (threadIdx.x == 0) batch_walk_query(B, qw);
+    batch_walk_query_copy(B, qw, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) batch_walk_query_reduce(B, qw);
     __syncthreads();
     if (B.trail) {
         trailing_tables_block(B.q, B.trail, (uint64_t*)(b.arena + B.off_T3),
@@ -102,14 +112,19 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b)
 }
 
 // The query of item `it`: the last q with item0[q] <= it (queries without
-// items share their successor's item0 and are never the last such q).
-FS_D int batch_query_of(const BatchDev& b, uint64_t it)
+// items share their successor's item0 and are never the last such q).  A
+// 32-way search by the calling warp (item0 never decreases; item0[0] = 0):
+// each round the lanes probe 32 evenly spaced queries at once.
+FS_D int batch_query_of(const BatchDev& b, uint64_t it, int lane)
 {
-    int lo = 0, hi = b.nq;  // answer in [lo, hi)
+    int lo = 0, hi = b.nq;  // answer in [lo, hi), item0[lo] <= it
     while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (b.qs[mid].item0 <= it) lo = mid;
-        else hi = mid;
+        const int step = (hi - lo + 31) >> 5;
+        const int probe = lo + lane * step;
+        const bool ok = probe < hi && b.qs[probe].item0 <= it;
+        const unsigned m = __ballot_sync(FULL, ok);  // lane 0 always
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
@@ -124,11 +139,13 @@ __global__ void __launch_bounds__(256) k_batch_starts(BatchDev b)
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     int cur = -1;
     for (uint64_t it = gw; it < items; it += nw) {
-        const int j = batch_query_of(b, it);
+        const int j = batch_query_of(b, it, lane);
         const BatchQ& B = b.qs[j];
         if (j != cur) {
             __syncwarp();
-            if (lane == 0) batch_walk_query(B, qw);
+            batch_walk_query_copy(B, qw, lane, 32);
+            __syncwarp();
+            if (lane == 0) batch_walk_query_reduce(B, qw);
             __syncwarp();
             cur = j;
         }
